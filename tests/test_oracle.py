@@ -1,0 +1,256 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: hand-
+computed values, closed forms, proved inequalities, exact special-case
+solvers and brute force.  A dropped term, a wrong sign or index, or a
+transposed operand in oracle/mm.py breaks at least one of them.
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import flr_inputs as fi
+from oracle import exact, mm
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _frac(a):
+    return np.array([[float(Fraction(v)) for v in row] for row in a]) if isinstance(a[0], list) \
+        else np.array([float(Fraction(v)) for v in a])
+
+
+@pytest.fixture(scope="module")
+def hand():
+    with open(os.path.join(GOLD, "hand_p3.json")) as fh:
+        return json.load(fh)
+
+
+# --------------------------------------------------------------------------- hand example
+def test_hand_objective(hand):
+    X, y, b = np.array(hand["X"], float), np.array(hand["y"], float), np.array(hand["beta"])
+    E = np.array(hand["edges"])
+    f = mm.objective(X, y, b, hand["lam1"], hand["lam2"], E)
+    assert f == pytest.approx(float(Fraction(hand["f"])), rel=1e-15)
+    fe = mm.objective_eps(X, y, b, hand["lam1"], hand["lam2"], E, hand["eps"])
+    assert fe == pytest.approx(hand["f_eps"], rel=1e-14)
+
+
+def test_hand_weights_and_system(hand):
+    X, y, b = np.array(hand["X"], float), np.array(hand["y"], float), np.array(hand["beta"])
+    E = np.array(hand["edges"])
+    a, w = mm.mm_weights(b, E, hand["eps"])
+    np.testing.assert_allclose(a, _frac(hand["a"]), rtol=1e-15)
+    np.testing.assert_allclose(w, _frac(hand["w"]), rtol=1e-15)
+    Q = mm.surrogate_matrix(X.T @ X, a, w, E, hand["lam1"], hand["lam2"])
+    np.testing.assert_allclose(Q, _frac(hand["Q"]), rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(X.T @ y, _frac(hand["c"]))
+    np.testing.assert_allclose(mm.init_beta(X, y), _frac(hand["beta0"]), rtol=1e-15)
+
+
+def test_init_zero_column():
+    X = np.array([[1.0, 0.0], [2.0, 0.0]])
+    y = np.array([1.0, 1.0])
+    np.testing.assert_allclose(mm.init_beta(X, y), [3.0 / 5.0, 0.0])
+
+
+# --------------------------------------------------------------------------- Proposition 1
+def _small(seed=0, n=7, p=6, kind="chain"):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, p))
+    y = rng.standard_normal(n)
+    E = fi.chain_edges(p) if kind == "chain" else fi.lattice_edges(2, p // 2)
+    return X, y, E
+
+
+@pytest.mark.parametrize("kind", ["chain", "lattice"])
+def test_majorizer_dominates_and_touches(kind):
+    """g_eps(b | b0) >= f_eps(b) with equality at b = b0 (Prop. 1(iii))."""
+    X, y, E = _small(1, kind=kind)
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        b0 = rng.standard_normal(X.shape[1]) * rng.choice([1e-3, 1.0])
+        b = b0 + rng.standard_normal(X.shape[1]) * rng.choice([1e-4, 0.1, 3.0])
+        for eps in (1e-6, 1e-2):
+            g = mm.majorizer(X, y, b, b0, 0.3, 0.7, E, eps)
+            fe = mm.objective_eps(X, y, b, 0.3, 0.7, E, eps)
+            assert g >= fe - 1e-10 * max(1.0, abs(fe))
+            assert mm.majorizer(X, y, b0, b0, 0.3, 0.7, E, eps) == pytest.approx(
+                mm.objective_eps(X, y, b0, 0.3, 0.7, E, eps), rel=1e-13)
+
+
+def test_system_is_hessian_of_majorizer():
+    """The Hessian of g_eps(. | b0) is X^T X + lam1 A + lam2 B (Appendix A.1)."""
+    X, y, E = _small(3, kind="lattice")
+    p = X.shape[1]
+    rng = np.random.default_rng(4)
+    b0 = rng.standard_normal(p)
+    eps, l1, l2 = 1e-3, 0.4, 0.9
+    a, w = mm.mm_weights(b0, E, eps)
+    Q = mm.surrogate_matrix(X.T @ X, a, w, E, l1, l2)
+    h = 1e-3
+    H = np.zeros((p, p))
+    g = lambda b: mm.majorizer(X, y, b, b0, l1, l2, E, eps)  # noqa: E731
+    base = b0 + 0.5
+    for i in range(p):
+        for j in range(p):
+            ei, ej = np.eye(p)[i] * h, np.eye(p)[j] * h
+            H[i, j] = (g(base + ei + ej) - g(base + ei - ej) - g(base - ei + ej)
+                       + g(base - ei - ej)) / (4 * h * h)
+    np.testing.assert_allclose(H, Q, rtol=1e-6, atol=1e-6)
+
+
+def test_surrogate_minimiser_has_zero_gradient():
+    """Q^-1 X^T y is the stationary point of g_eps(. | b0) (Eq. lin-sys)."""
+    X, y, E = _small(5)
+    p = X.shape[1]
+    b0 = np.random.default_rng(6).standard_normal(p)
+    eps, l1, l2 = 1e-2, 0.2, 0.5
+    a, w = mm.mm_weights(b0, E, eps)
+    Q = mm.surrogate_matrix(X.T @ X, a, w, E, l1, l2)
+    b = np.linalg.solve(Q, X.T @ y)
+    h = 1e-5
+    for i in range(p):
+        e = np.eye(p)[i] * h
+        d = (mm.majorizer(X, y, b + e, b0, l1, l2, E, eps)
+             - mm.majorizer(X, y, b - e, b0, l1, l2, E, eps)) / (2 * h)
+        assert abs(d) < 1e-7
+
+
+def test_eps_bound_holds():
+    """0 <= f - f_eps = eps-log terms (Appendix A.1, part (ii))."""
+    X, y, E = _small(7)
+    rng = np.random.default_rng(8)
+    for _ in range(20):
+        b = rng.standard_normal(X.shape[1])
+        f = mm.objective(X, y, b, 0.3, 0.6, E)
+        fe = mm.objective_eps(X, y, b, 0.3, 0.6, E, 1e-3)
+        assert f >= fe
+        assert f - fe == pytest.approx(mm.eps_gap(b, 0.3, 0.6, E, 1e-3), rel=1e-10)
+
+
+# --------------------------------------------------------------------------- Algorithm 1
+def test_mm_monotone_descent_of_perturbed_objective():
+    """f_eps(b^(r+1)) <= f_eps(b^(r)) at every MM iteration (Lemma 2)."""
+    pr = fi.config(1)
+    r = mm.mm_dense(pr.X64(), pr.y, pr.graph.edges, pr.lam1, pr.lam2, pr.eps,
+                    tol=1e-10, max_iter=400)
+    fe = np.array(r.feps_trace)
+    assert np.all(np.diff(fe) <= 1e-12 * np.abs(fe[:-1]))
+
+
+def test_mm_soft_threshold_when_X_identity_and_no_fusion():
+    """X = I, lam2 = 0: the minimiser is S(y, lam1) (Eq. soft; Hunter-Li lasso MM)."""
+    rng = np.random.default_rng(9)
+    p = 30
+    y = rng.standard_normal(p) * 2
+    eps, lam1 = 1e-8, 0.7
+    r = mm.mm_dense(np.eye(p), y, fi.chain_edges(p), lam1, 0.0, eps, tol=1e-15, max_iter=3000)
+    b = exact.soft_threshold(y, lam1)
+    # the perturbed minimiser differs from the exact one by O(eps) per coordinate
+    np.testing.assert_allclose(r.beta, b, atol=1e-6)
+    f_star = mm.objective(np.eye(p), y, b, lam1, 0.0, fi.chain_edges(p))
+    assert f_star <= r.f <= f_star + mm.eps_gap(r.beta, lam1, 0.0, fi.chain_edges(p), eps) + 1e-10
+
+
+def test_mm_least_squares_when_unpenalised():
+    """lam1 = lam2 = 0 and n > p: one MM step solves the normal equations."""
+    rng = np.random.default_rng(10)
+    X = rng.standard_normal((40, 12))
+    y = rng.standard_normal(40)
+    r = mm.mm_dense(X, y, fi.chain_edges(12), 0.0, 0.0, 1e-6, tol=1e-14, max_iter=3)
+    np.testing.assert_allclose(r.beta, exact.least_squares(X, y), rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("lam1,lam2", [(0.0, 0.5), (0.3, 0.8), (0.05, 2.0)])
+def test_mm_matches_exact_flsa_on_chain(lam1, lam2):
+    """X = I, chain E: MM reaches the exact 1D FLSA optimum within the eps certificate."""
+    rng = np.random.default_rng(11)
+    p = 60
+    y = np.repeat(rng.standard_normal(6) * 2, 10) + 0.3 * rng.standard_normal(p)
+    E = fi.chain_edges(p)
+    eps = 1e-7
+    b_star = exact.flsa_chain(y, lam1, lam2)
+    f_star = mm.objective(np.eye(p), y, b_star, lam1, lam2, E)
+    r = mm.mm_dense(np.eye(p), y, E, lam1, lam2, eps, tol=1e-15, max_iter=20000)
+    slack = mm.eps_gap(r.beta, lam1, lam2, E, eps)
+    assert f_star - 1e-12 <= r.f <= f_star + slack + 1e-9 * f_star
+    assert np.abs(r.beta - b_star).max() < 1e-3
+
+
+def test_exact_flsa_against_brute_force():
+    """The DP FLSA solver agrees with face enumeration (two independent exact solvers)."""
+    rng = np.random.default_rng(12)
+    for _ in range(4):
+        p = 5
+        y = rng.standard_normal(p)
+        for lam1, lam2 in [(0.0, 0.4), (0.2, 0.3), (0.5, 1.2)]:
+            b1 = exact.flsa_chain(y, lam1, lam2)
+            b2, f2 = exact.brute_force(np.eye(p), y, lam1, lam2, fi.chain_edges(p))
+            np.testing.assert_allclose(b1, b2, atol=1e-12)
+            assert exact.kkt_residual(np.eye(p), y, b1, lam1, lam2, fi.chain_edges(p)) < 1e-10
+
+
+@pytest.mark.parametrize("kind,seed", [("chain", 13), ("lattice", 14), ("chain", 15)])
+def test_mm_matches_brute_force(kind, seed):
+    """General X (n >= p): MM objective within the certificate of the brute-force optimum."""
+    rng = np.random.default_rng(seed)
+    p = 4
+    X = rng.standard_normal((6, p))
+    y = X @ np.array([1.0, 1.0, 0.0, -0.5]) + 0.3 * rng.standard_normal(6)
+    E = fi.chain_edges(p) if kind == "chain" else fi.lattice_edges(2, 2)
+    lam1, lam2, eps = 0.3, 0.5, 1e-8
+    b_star, f_star = exact.brute_force(X, y, lam1, lam2, E)
+    assert exact.kkt_residual(X, y, b_star, lam1, lam2, E) < 1e-9
+    r = mm.mm_dense(X, y, E, lam1, lam2, eps, tol=1e-15, max_iter=20000)
+    assert f_star - 1e-12 <= r.f <= f_star + mm.eps_gap(r.beta, lam1, lam2, E, eps) + 1e-10
+    np.testing.assert_allclose(r.beta, b_star, atol=1e-4)
+
+
+def test_fixed_point_is_stationary():
+    """At the MM limit the perturbed gradient vanishes (Lemma 2): Q(b) b = X^T y."""
+    pr = fi.config(1, scale=0.3)
+    X, E = pr.X64(), pr.graph.edges
+    r = mm.mm_dense(X, pr.y, E, pr.lam1, pr.lam2, pr.eps, tol=1e-15, max_iter=20000)
+    g = mm.surrogate_gradient(X, pr.y, r.beta, pr.lam1, pr.lam2, E, pr.eps)
+    assert np.linalg.norm(g) <= 1e-5 * np.linalg.norm(X.T @ pr.y)
+
+
+@pytest.mark.parametrize("kind", ["chain", "lattice"])
+def test_woodbury_oracle_matches_dense(kind):
+    """Oracle-B takes the same iterates as Algorithm 1 with a dense Cholesky."""
+    if kind == "chain":
+        pr = fi.config(1)
+    else:
+        pr = fi.config(2, scale=0.05)
+    X, E = pr.X64(), pr.graph.edges
+    r1 = mm.mm_dense(X, pr.y, E, pr.lam1, pr.lam2, pr.eps, tol=0, max_iter=60, stall_stop=False)
+    r2 = mm.mm_woodbury(X, pr.y, E, pr.lam1, pr.lam2, pr.eps, tol=0, max_iter=60, stall_stop=False)
+    np.testing.assert_allclose(r2.f_trace, r1.f_trace, rtol=1e-10)
+    np.testing.assert_allclose(r2.beta, r1.beta, atol=1e-7 * np.abs(r1.beta).max())
+
+
+# --------------------------------------------------------------------------- inputs
+def test_bf16_rounding_is_nearest_even():
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -2.5, 1.0 + 2 ** -7 + 2 ** -9],
+                 dtype=np.float32)
+    back = fi.bf16_bits_to_f64(fi.f32_to_bf16_bits(x))
+    np.testing.assert_array_equal(back, [1.0, 1.0, 1.0 + 4 * 2 ** -8, -2.5, 1.0 + 2 ** -7])
+
+
+def test_graph_sizes():
+    assert fi.chain_edges(200).shape == (199, 2)
+    assert fi.lattice_edges(100, 100).shape == (19800, 2)
+    assert fi.lattice_edges(250, 400).shape == (250 * 399 + 249 * 400, 2)
+    e = fi.knn_edges(np.random.default_rng(0).uniform(size=(300, 2)), 5)
+    assert np.all(e[:, 0] < e[:, 1]) and len(np.unique(e, axis=0)) == len(e)
+
+
+def test_configs_shapes():
+    p1 = fi.config(1)
+    assert (p1.n, p1.p, p1.dtype, p1.graph.m) == (100, 200, "f64", 199)
+    p2 = fi.config(2, scale=0.04)
+    assert p2.dtype == "f32" and p2.graph.kind == "lattice"
