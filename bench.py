@@ -1,0 +1,343 @@
+"""Benchmark: fused lasso regression solves per second on one GB300.
+
+A step is one complete MM solve (Algorithms 1-2 with the PCG inner solve) of
+the 2D-lattice workload: q = 100 (p = 10,000), n = 1000, X iid N(0,1) stored
+FP32, lambda = (0.05, 0.2), eps = 1e-6, synthetic data from flr_inputs.  The
+solve stops on the MM relative-change test; its objective is checked
+against the stored FP64 oracle solution (relative gap <= 1e-6).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl flr|reference]
+
+N > 1 (torchrun): independent replicas, one per GPU (the solve does not
+shard), each rank on its own dataset seed; value = all ranks' solves / max time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="lattice-fp32-q100-n1000", config=2, q=100, n=1000, p=10000,
+                lam1=0.05, lam2=0.2, eps=1e-6)
+METRIC = "FLR solves/s at obj gap<=1e-6 (lattice q=100, n=1000, FP32 X)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="flr", choices=["flr", "reference"])
+    ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--tol-cg", type=float, default=1e-8)
+    ap.add_argument("--precond", default="jacobi")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_golden():
+    path = os.path.join(ROOT, "tests", "golden", "config2.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1306_1970_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", "mm_solve_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                                 else "_work", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(st, n, p, m, bx):
+    """Bytes one solve must move at minimum: every Q-apply (one per CG iteration plus the
+    CG start of each MM iteration) reads X once and touches its FP64 vectors."""
+    per_apply = n * p * bx + 64 * p + 16 * m + 8 * n
+    return (st.cg_iters + st.mm_iters) * per_apply
+
+
+def cpu_baseline(pr, golden, budget_s):
+    """The FP64 oracle (Algorithm 1, Woodbury-solved surrogate) timed on a bounded sample:
+    as many MM iterations as fit in ~budget_s, scaled to the oracle's iterations to gap 1e-6."""
+    from oracle import mm
+    X = pr.X64()
+    E = pr.graph.edges
+    t0 = time.perf_counter()
+    mm.mm_woodbury(X, pr.y, E, pr.lam1, pr.lam2, pr.eps, tol=0.0, max_iter=1, stall_stop=False)
+    t1 = time.perf_counter()
+    per_iter = t1 - t0
+    k = max(1, int(budget_s / max(per_iter, 1e-3)) - 1)
+    t0 = time.perf_counter()
+    mm.mm_woodbury(X, pr.y, E, pr.lam1, pr.lam2, pr.eps, tol=0.0, max_iter=k, stall_stop=False)
+    per_iter = (time.perf_counter() - t0) / k
+    iters = None
+    if golden is not None:
+        iters = golden.get("iters_to_gap_1e-6")
+    return per_iter, k, iters
+
+
+def run_reference(args, rank):
+    """The oracle (CPU, FP64) on this workload, each step a bounded sample."""
+    import flr_inputs as fi
+    if rank != 0:
+        return
+    golden = load_golden()
+    pr = fi.config(2)
+    per_iter, k, iters = cpu_baseline(pr, golden, args.cpu_seconds / max(1, args.steps))
+    if iters is None:
+        iters = 1000
+    value = 1.0 / (per_iter * iters)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_iter * iters * 1000.0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["workload"], "solver": "oracle MM, Woodbury surrogate solve"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{k} MM iterations of the oracle, scaled to {iters} "
+                                       f"iterations to obj gap 1e-6"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    import flr_inputs as fi
+    import paper_1306_1970_gb300 as flr
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    flr.load(build_if_missing=True)
+
+    pr = fi.config(2, s=rank)
+    golden = load_golden() if rank == 0 else None
+    Xh = torch.from_numpy(pr.X).pin_memory()
+    yh = torch.from_numpy(pr.y).pin_memory()
+    X, y = Xh.to(dev), yh.to(dev)
+    prob = flr.Problem(X, y, pr.graph)
+    opts = flr.default_opts(precond=args.precond, tol_cg=args.tol_cg, max_mm=20000)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty(pr.p, dtype=torch.float64, device=dev)
+
+    def solve():
+        return prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=args.tol, out=out, opts=opts)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        solve()
+    torch.cuda.synchronize()
+
+    # ---- device-timed solves (inputs resident in HBM, L2 flushed between steps)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    stats = []
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            _, st = solve()
+            evs[k][1].record(stream)
+            stats.append(st)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_dev = sum(step_ms) / 1000.0
+    if pg:
+        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_dev = float(t.item())
+        pg.barrier()
+    value = world * args.steps / t_dev
+
+    # ---- end to end through the C ABI with host buffers: create from pinned host X, y,
+    #      solve, beta back to pinned host memory, destroy -- all inside the timed region
+    beta_h = torch.empty(pr.p, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        flush.fill_(2.0)
+        ph = flr.Problem(Xh, yh, pr.graph)
+        ph.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=args.tol, out=beta_h, opts=opts)
+        ph.close()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / 1000.0
+    if pg:
+        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = world * e2e_steps / t_e2e
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+
+    # ---- parity of the timed solves against the stored oracle solution
+    st = stats[-1]
+    gap = None
+    if golden is not None:
+        gap = max(abs(s.f - golden["f"]) / golden["f"] for s in stats)
+    # ---- roofline of the solve kernel (one launch per solve)
+    bx = 4
+    kern_ms = [s.ms for s in stats]
+    alg = [algorithmic_bytes(s, pr.n, pr.p, pr.graph.m, bx) for s in stats]
+    achieved = sum(alg) / (sum(kern_ms) / 1000.0) / 1e9
+    peak, peak_kind = measured_peaks()
+    tr = ncu_traffic()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind,
+            "traffic": tr["dram_bytes_per_launch_scaled"] if tr else None,
+            "kernel": "mm_solve_kernel<float, stencil>",
+            "algorithmic_bytes_per_launch": float(np.mean(alg)),
+            "note": "X (40 MB) stays L2-resident across the CG iterations of one solve"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        per_iter, k, iters = cpu_baseline(pr, golden, args.cpu_seconds)
+        if iters is None:
+            iters = st.mm_iters
+        cpu = {"value": 1.0 / (per_iter * iters), "unit": "solves/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"{k} MM iterations of the FP64 oracle (Woodbury surrogate solve) on "
+                         f"this workload, scaled to {iters} MM iterations to obj gap 1e-6"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_dev / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD["workload"], "n": pr.n, "p": pr.p, "m": pr.graph.m,
+                   "lam1": pr.lam1, "lam2": pr.lam2, "eps": pr.eps, "tol": args.tol,
+                   "tol_cg": args.tol_cg, "precond": args.precond, "l2": "flushed between steps",
+                   "mm_iters": st.mm_iters, "cg_iters": st.cg_iters, "grid": st.grid,
+                   "obj_gap_vs_oracle": gap, "parallelism": f"replicas{world}"},
+        "e2e": {"value": e2e_value, "unit": "solves/s",
+                "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size() + yh.numel() * 8),
+                "d2h_bytes_per_step": int(pr.p * 8)},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "wall_s_timed": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

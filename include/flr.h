@@ -1,0 +1,179 @@
+/*
+ * flr.h -- C ABI of the GB300 fused lasso regression (FLR) solver.
+ *
+ * Problem (Section 1, Eq. obj):
+ *     minimise  f(beta) = 1/2 ||y - X beta||^2 + lambda1 sum_j |beta_j|
+ *                         + lambda2 sum_{(j,k) in E} |beta_j - beta_k|
+ * solved by the majorization-minimization (MM) iteration of Section 3:
+ * each MM iteration r reweights a_j = 1/(|beta_j| + eps) and
+ * w_jk = 1/(|beta_j - beta_k| + eps) from the current iterate and solves the
+ * symmetric positive-definite surrogate system (Eq. lin-sys)
+ *     (X^T X + lambda1 A(r) + lambda2 B(r)) beta = X^T y
+ * by preconditioned conjugate gradient warm-started at beta(r)
+ * (Algorithm 2), until the relative change of f is at most tol
+ * (Algorithm 1/2 outer stop).  The limit minimises the perturbed objective
+ * f_eps of Eq. pert.
+ *
+ * Conventions for every entry point:
+ *   - Return values are flr_status codes; nothing is thrown across the ABI
+ *     and nothing aborts.  flr_strerror() names a code.
+ *   - "device" pointers are CUDA global-memory pointers on the current
+ *     device; "host" pointers are ordinary (preferably pinned) host memory.
+ *   - A handle is bound to the CUDA device that was current at flr_create
+ *     and to the stream given there.  All work of a handle is issued on
+ *     that stream.  A handle is not thread-safe; distinct handles are
+ *     independent.
+ *   - All reals are IEEE double unless the storage dtype of X says
+ *     otherwise.
+ */
+#ifndef FLR_H
+#define FLR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum flr_status {
+    FLR_OK = 0,
+    FLR_EINVAL = 1,       /* invalid argument (sizes, pointers, edge set, lambdas, eps, tol) */
+    FLR_ENOMEM = 2,       /* a device or pinned-host allocation failed */
+    FLR_ECUDA = 3,        /* a CUDA runtime call failed (launch, copy, device query) */
+    FLR_ENOTCONV = 4,     /* max_mm MM iterations reached before the outer stop test held */
+    FLR_EBREAKDOWN = 5,   /* CG met p^T Q p <= 0 (Q not SPD, e.g. lambda1 = 0 with singular X^T X + lambda2 B) */
+    FLR_ENONFINITE = 6,   /* a non-finite value appeared (inputs or arithmetic) */
+    FLR_ETIMEOUT = 7,     /* a bounded device-side wait gave up; results are not valid */
+    FLR_ENOTIMPL = 8      /* the requested combination is not implemented */
+} flr_status;
+
+/* Storage type of X.  Products with X accumulate in FP32 for F32/BF16/F16
+ * and in FP64 for F64; every other quantity is FP64. */
+typedef enum flr_dtype { FLR_F64 = 0, FLR_F32 = 1, FLR_BF16 = 2, FLR_F16 = 3 } flr_dtype;
+
+/* Where the pointers passed to flr_create / flr_solve live. */
+typedef enum flr_mem { FLR_MEM_DEVICE = 0, FLR_MEM_HOST = 1 } flr_mem;
+
+/* The edge set E (Section 1).
+ *   FLR_E_CHAIN:   E = {(j-1, j) : j = 1..p-1}, the standard FLR.  q1, q2,
+ *                  edges, m are ignored.
+ *   FLR_E_LATTICE: the two-dimensional FLR on a q1 x q2 lattice; coefficient
+ *                  (i, j) has index i*q2 + j (row-major) and E holds the
+ *                  horizontal and vertical neighbour pairs.  q1*q2 must equal p.
+ *   FLR_E_EDGES:   an explicit list: `edges` holds m pairs (j, k) as 2*m
+ *                  int64 values, 0-based, j != k, no pair listed twice in
+ *                  either orientation (E is a set).  m = 0 is allowed. */
+typedef enum flr_graph_kind { FLR_E_CHAIN = 0, FLR_E_LATTICE = 1, FLR_E_EDGES = 2 } flr_graph_kind;
+
+typedef struct flr_graph {
+    int32_t kind;           /* flr_graph_kind */
+    int32_t reserved;
+    int64_t q1, q2;         /* lattice shape */
+    const int64_t* edges;   /* FLR_E_EDGES: 2*m values, in the memory named by flr_create's `mem` */
+    int64_t m;
+} flr_graph;
+
+/* Preconditioner M of the inner PCG (Algorithm 2).  The preconditioner
+ * changes the number of CG iterations, not the MM iterates' limit.
+ *   FLR_PC_JACOBI:  M = diag(X^T X + lambda1 A + lambda2 B).
+ *   FLR_PC_TRIDIAG: M = the tridiagonal part of X^T X + lambda1 A + lambda2 B
+ *                   over consecutive indices, with diag(X^T X) in place of
+ *                   X^T X; solved exactly within each block of consecutive
+ *                   indices owned by one thread block (blocks decouple at
+ *                   their ends).  On a chain this is the paper's tridiagonal
+ *                   preconditioner plus diag(X^T X); on a lattice it is a
+ *                   horizontal-line preconditioner.
+ *   FLR_PC_PAPER:   as TRIDIAG but without diag(X^T X): M = lambda1 A + lambda2 B
+ *                   restricted to consecutive-index couplings (Algorithm 2).
+ *   FLR_PC_AUTO:    TRIDIAG for chains, JACOBI otherwise. */
+typedef enum flr_precond {
+    FLR_PC_AUTO = 0, FLR_PC_JACOBI = 1, FLR_PC_TRIDIAG = 2, FLR_PC_PAPER = 3
+} flr_precond;
+
+typedef struct flr_opts {
+    int32_t max_mm;      /* MM iteration cap (default 10000, Section 5) */
+    int32_t max_cg;      /* CG iterations per MM iteration (default 10000) */
+    int32_t min_cg;      /* at least this many CG iterations per MM iteration (default 1) */
+    int32_t precond;     /* flr_precond (default FLR_PC_AUTO) */
+    double tol_cg;       /* inner stop ||r_j|| / ||X^T y|| <= tol_cg (default: tol, as Algorithm 2) */
+    int32_t grid;        /* thread blocks of the solve kernel; 0 = automatic */
+    int32_t inject_stall;/* test hook: 1 = block 0 leaves before the first grid barrier, so
+                            the other blocks' bounded waits expire and the solve returns
+                            FLR_ETIMEOUT (needs grid >= 2).  0 in normal use. */
+    int64_t wait_cycles; /* bound of every device-side wait in SM clock cycles (0 = 2^33) */
+    int32_t reserved[4];
+} flr_opts;
+
+typedef struct flr_stats {
+    int32_t mm_iters;        /* MM iterations performed */
+    int32_t cg_iters;        /* CG iterations summed over all MM iterations */
+    int32_t status;          /* flr_status of the solve */
+    int32_t grid;            /* thread blocks used */
+    double f;                /* f(beta) at the returned beta (Eq. obj) */
+    double f_eps;            /* f_eps(beta) (Eq. pert) */
+    double rel_change;       /* last |f(b_new) - f(b_old)| / |f(b_old)| */
+    double cg_relres;        /* ||r|| / ||X^T y|| at the end of the last inner solve */
+    double ms;               /* device time of the solve kernel, milliseconds */
+} flr_stats;
+
+typedef struct flr_handle flr_handle;
+typedef flr_handle* flr_t;
+
+/* Fill *opts with the defaults listed in flr_opts. */
+void flr_default_opts(flr_opts* opts);
+
+/* Create a problem handle.
+ *   X      n x p design matrix, row-major, row stride ldx >= p elements,
+ *          element type `dtype` (FLR_BF16 / FLR_F16: 16-bit patterns).
+ *   y      n responses (double).
+ *   E      edge set (see flr_graph); E->edges in the memory named by `mem`.
+ *   mem    FLR_MEM_DEVICE or FLR_MEM_HOST: where X, y and E->edges live.
+ *   stream cudaStream_t (NULL = legacy default stream).
+ * The handle copies what it needs (X into a column-major layout of the
+ * same dtype, y, the edge set) and computes X^T y and diag(X^T X) in FP64;
+ * the caller's buffers may be released once this call returns.
+ * Errors: FLR_EINVAL for n < 1, p < 1, ldx < p, a null pointer, an
+ * unknown dtype or kind, q1*q2 != p, an edge index outside [0, p), a self
+ * loop or a repeated pair; FLR_ENOMEM / FLR_ECUDA as named. */
+flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_t ldx,
+                      const double* y, const flr_graph* E, int32_t mem, void* stream,
+                      flr_t* out);
+
+/* Run the MM iteration for one (lambda1, lambda2).
+ *   eps        perturbation constant of Eq. pert (> 0).
+ *   tol        outer stop: |f(b(r+1)) - f(b(r))| / |f(b(r))| <= tol (> 0).
+ *   opts       NULL for defaults.
+ *   beta_init  NULL: beta(0)_j = X_j^T y / X_j^T X_j (0 for a zero column;
+ *              Algorithm 1); else p doubles in `io_mem` memory.
+ *   beta_out   p doubles in `io_mem` memory (may equal beta_init).
+ *   io_mem     FLR_MEM_DEVICE or FLR_MEM_HOST for beta_init and beta_out.
+ *   stats      optional (NULL allowed), host memory.
+ * lambda1 = 0 is accepted; the surrogate system is then SPD only when
+ * X^T X + lambda2 B is, otherwise FLR_EBREAKDOWN.  Returns FLR_ENOTCONV
+ * (with beta_out written) when max_mm is reached.  The call returns after
+ * the solve has finished on the handle's stream. */
+flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double tol,
+                     const flr_opts* opts, const double* beta_init, double* beta_out,
+                     int32_t io_mem, flr_stats* stats);
+
+/* Solve K independent (lambda1[k], lambda2[k]) problems on the same X, y, E
+ * (a lambda grid).  betas is p x K column-major (column k = beta for pair k)
+ * in `io_mem` memory; objectives (K doubles) and stats (K entries) are host
+ * memory and optional.  Returns the first non-OK status over k, else FLR_OK. */
+flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const double* lambda2,
+                           double eps, double tol, const flr_opts* opts, double* betas,
+                           int32_t io_mem, double* objectives, flr_stats* stats);
+
+/* Release a handle and everything it owns (NULL is ignored). */
+void flr_destroy(flr_t h);
+
+/* Static, NUL-terminated name and description of a status code. */
+const char* flr_strerror(int32_t status);
+
+/* Problem sizes of a handle (any out-pointer may be NULL). */
+flr_status flr_get_info(flr_t h, int64_t* n, int64_t* p, int64_t* m, int32_t* dtype);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLR_H */

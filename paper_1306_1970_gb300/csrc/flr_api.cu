@@ -1,0 +1,499 @@
+// C ABI of the fused lasso regression solver (see include/flr.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/flr.h"
+#include "flr_solve.cuh"
+
+using namespace flr;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// setup kernels
+// ---------------------------------------------------------------------------
+// Xt[j * ldn + i] = X[i * ldx + j]  (32 x 32 tiles through shared memory)
+template <typename T>
+__global__ void transpose_kernel(const T* __restrict__ X, long long n, long long p, long long ldx,
+                                 T* __restrict__ Xt, long long ldn) {
+  __shared__ T tile[32][33];
+  const long long i0 = (long long)blockIdx.y * 32, c0 = (long long)blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const long long i = i0 + r, j = c0 + threadIdx.x;
+    if (i < n && j < p) tile[r][threadIdx.x] = X[i * ldx + j];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const long long j = c0 + r, i = i0 + threadIdx.x;
+    if (j < p && i < n) Xt[j * ldn + i] = tile[threadIdx.x][r];
+  }
+}
+
+template <typename TX> __device__ __forceinline__ double widen(TX v);
+template <> __device__ __forceinline__ double widen<double>(double v) { return v; }
+template <> __device__ __forceinline__ double widen<float>(float v) { return (double)v; }
+template <> __device__ __forceinline__ double widen<__nv_bfloat16>(__nv_bfloat16 v) {
+  return (double)__bfloat162float(v);
+}
+template <> __device__ __forceinline__ double widen<__half>(__half v) {
+  return (double)__half2float(v);
+}
+
+// d_j = X_j^T X_j and c_j = X_j^T y in FP64 (one warp per column)
+template <typename TX>
+__global__ void colstats_kernel(const TX* __restrict__ Xt, const double* __restrict__ y,
+                                long long n, long long p, long long ldn, double* d, double* c) {
+  const int lane = threadIdx.x & 31;
+  const long long j = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (j >= p) return;
+  const TX* col = Xt + j * ldn;
+  double sd = 0.0, sc = 0.0;
+  for (long long i = lane; i < n; i += 32) {
+    const double v = widen<TX>(col[i]);
+    sd = fma(v, v, sd);
+    sc = fma(v, y[i], sc);
+  }
+  sd = warp_sum(sd);
+  sc = warp_sum(sc);
+  if (lane == 0) { d[j] = sd; c[j] = sc; }
+}
+
+size_t dtype_size(int dt) {
+  switch (dt) {
+    case FLR_F64: return 8;
+    case FLR_F32: return 4;
+    case FLR_BF16: case FLR_F16: return 2;
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct flr_handle {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  int dtype = 0;
+  long long n = 0, p = 0, ldn = 0, m = 0;
+  int gkind = FLR_E_CHAIN;
+  long long q1 = 1, q2 = 0;
+  void* Xt = nullptr;
+  double *y = nullptr, *c = nullptr, *d = nullptr;
+  double cnorm = 0.0;
+  long long* rowptr = nullptr;
+  int* col = nullptr;
+  // solve workspace
+  double *x = nullptr, *r = nullptr, *z = nullptr, *pb0 = nullptr, *pb1 = nullptr, *q = nullptr,
+         *a = nullptr, *wL = nullptr, *wR = nullptr, *wU = nullptr, *wD = nullptr, *wc = nullptr,
+         *idg = nullptr, *K1 = nullptr, *K2 = nullptr, *binv = nullptr, *part = nullptr;
+  void* ub0 = nullptr;
+  void* ub1 = nullptr;
+  unsigned char* ctl = nullptr;     // barrier counter, error flag, DevStats
+  unsigned char* hctl = nullptr;    // pinned copy of ctl
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+constexpr int kMaxGrid = 512;       // grid reductions use one thread per block
+
+flr_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return FLR_OK;
+  if (e == cudaErrorMemoryAllocation) return FLR_ENOMEM;
+  return FLR_ECUDA;
+}
+
+#define FLR_TRY(expr)                                   \
+  do {                                                  \
+    cudaError_t _e = (expr);                            \
+    if (_e != cudaSuccess) {                            \
+      (void)cudaGetLastError();                         \
+      return cuda_status(_e);                           \
+    }                                                   \
+  } while (0)
+
+template <typename T>
+flr_status dalloc(flr_handle* h, T** out, size_t count) {
+  void* ptr = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+  if (e != cudaSuccess) { (void)cudaGetLastError(); return FLR_ENOMEM; }
+  h->allocs.push_back(ptr);
+  *out = static_cast<T*>(ptr);
+  return FLR_OK;
+}
+
+void release(flr_handle* h) {
+  if (!h) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->hctl) cudaFreeHost(h->hctl);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  cudaSetDevice(prev);
+  delete h;
+}
+
+template <typename TX>
+void launch_setup(flr_handle* h, const void* Xsrc, long long ldx) {
+  dim3 tb(32, 8);
+  dim3 grid((unsigned)((h->p + 31) / 32), (unsigned)((h->n + 31) / 32));
+  using Raw = typename std::conditional<sizeof(TX) == 8, unsigned long long,
+              typename std::conditional<sizeof(TX) == 4, unsigned, unsigned short>::type>::type;
+  transpose_kernel<Raw><<<grid, tb, 0, h->stream>>>(static_cast<const Raw*>(Xsrc), h->n, h->p, ldx,
+                                                    static_cast<Raw*>(h->Xt), h->ldn);
+  const int wpb = 8;
+  colstats_kernel<TX><<<(unsigned)((h->p + wpb - 1) / wpb), wpb * 32, 0, h->stream>>>(
+      static_cast<const TX*>(h->Xt), h->y, h->n, h->p, h->ldn, h->d, h->c);
+}
+
+flr_status build_csr(flr_handle* h, const int64_t* edges_host, long long m) {
+  const long long p = h->p;
+  std::vector<std::pair<long long, long long>> pr;
+  pr.reserve((size_t)m);
+  for (long long e = 0; e < m; ++e) {
+    long long j = edges_host[2 * e], k = edges_host[2 * e + 1];
+    if (j < 0 || k < 0 || j >= p || k >= p || j == k) return FLR_EINVAL;
+    if (j > k) std::swap(j, k);
+    pr.emplace_back(j, k);
+  }
+  std::sort(pr.begin(), pr.end());
+  for (size_t i = 1; i < pr.size(); ++i)
+    if (pr[i] == pr[i - 1]) return FLR_EINVAL;
+  std::vector<long long> rowptr((size_t)p + 1, 0);
+  for (auto& e : pr) { rowptr[e.first + 1]++; rowptr[e.second + 1]++; }
+  for (long long j = 0; j < p; ++j) rowptr[j + 1] += rowptr[j];
+  std::vector<int> col((size_t)std::max<long long>(1, 2 * m));
+  std::vector<long long> fill(rowptr.begin(), rowptr.end() - 1);
+  for (auto& e : pr) {
+    col[fill[e.first]++] = (int)e.second;
+    col[fill[e.second]++] = (int)e.first;
+  }
+  for (long long j = 0; j < p; ++j) std::sort(col.begin() + rowptr[j], col.begin() + rowptr[j + 1]);
+  flr_status s;
+  if ((s = dalloc(h, &h->rowptr, (size_t)p + 1)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->col, (size_t)std::max<long long>(1, 2 * m))) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->wc, (size_t)std::max<long long>(1, 2 * m))) != FLR_OK) return s;
+  FLR_TRY(cudaMemcpy(h->rowptr, rowptr.data(), sizeof(long long) * (p + 1), cudaMemcpyHostToDevice));
+  FLR_TRY(cudaMemcpy(h->col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice));
+  return FLR_OK;
+}
+
+template <typename TX, int GK>
+flr_status launch_solve_t(flr_handle* h, SolveParams& P, int G, size_t smem) {
+  auto kern = mm_solve_kernel<TX, GK>;
+  FLR_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int nb = 0;
+  FLR_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem));
+  if (nb < 1 || G > nb * h->sm_count) return FLR_ENOTIMPL;
+  void* args[] = {(void*)&P};
+  FLR_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(kThreads), args, smem,
+                                      h->stream));
+  return FLR_OK;
+}
+
+flr_status launch_solve(flr_handle* h, SolveParams& P, int G, size_t smem) {
+  const int gk = h->gkind == FLR_E_EDGES ? GK_CSR : GK_STENCIL;
+  switch (h->dtype) {
+    case FLR_F64: return gk ? launch_solve_t<double, GK_CSR>(h, P, G, smem)
+                            : launch_solve_t<double, GK_STENCIL>(h, P, G, smem);
+    case FLR_F32: return gk ? launch_solve_t<float, GK_CSR>(h, P, G, smem)
+                            : launch_solve_t<float, GK_STENCIL>(h, P, G, smem);
+    case FLR_BF16: return gk ? launch_solve_t<__nv_bfloat16, GK_CSR>(h, P, G, smem)
+                             : launch_solve_t<__nv_bfloat16, GK_STENCIL>(h, P, G, smem);
+    case FLR_F16: return gk ? launch_solve_t<__half, GK_CSR>(h, P, G, smem)
+                            : launch_solve_t<__half, GK_STENCIL>(h, P, G, smem);
+  }
+  return FLR_EINVAL;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// public API
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void flr_default_opts(flr_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->max_mm = 10000;
+  o->max_cg = 10000;
+  o->min_cg = 1;
+  o->precond = FLR_PC_AUTO;
+  o->tol_cg = 0.0;
+  o->grid = 0;
+}
+
+const char* flr_strerror(int32_t s) {
+  switch (s) {
+    case FLR_OK: return "FLR_OK: success";
+    case FLR_EINVAL: return "FLR_EINVAL: invalid argument";
+    case FLR_ENOMEM: return "FLR_ENOMEM: out of memory";
+    case FLR_ECUDA: return "FLR_ECUDA: CUDA runtime error";
+    case FLR_ENOTCONV: return "FLR_ENOTCONV: MM iteration cap reached before the stop test held";
+    case FLR_EBREAKDOWN: return "FLR_EBREAKDOWN: CG breakdown (p^T Q p <= 0)";
+    case FLR_ENONFINITE: return "FLR_ENONFINITE: non-finite value";
+    case FLR_ETIMEOUT: return "FLR_ETIMEOUT: a bounded device-side wait gave up";
+    case FLR_ENOTIMPL: return "FLR_ENOTIMPL: combination not implemented";
+    default: return "unknown flr_status";
+  }
+}
+
+flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_t ldx,
+                      const double* y, const flr_graph* E, int32_t mem, void* stream,
+                      flr_t* out) {
+  if (!out) return FLR_EINVAL;
+  *out = nullptr;
+  if (!X || !y || !E || n < 1 || p < 1 || ldx < p) return FLR_EINVAL;
+  if (dtype_size(dtype) == 0) return FLR_EINVAL;
+  if (mem != FLR_MEM_DEVICE && mem != FLR_MEM_HOST) return FLR_EINVAL;
+  if (p >= (int64_t)INT32_MAX || n >= (int64_t)INT32_MAX) return FLR_ENOTIMPL;
+  long long q1 = 1, q2 = p, m = 0;
+  switch (E->kind) {
+    case FLR_E_CHAIN: m = p - 1; break;
+    case FLR_E_LATTICE:
+      if (E->q1 < 1 || E->q2 < 1 || E->q1 * E->q2 != p) return FLR_EINVAL;
+      q1 = E->q1; q2 = E->q2;
+      m = q1 * (q2 - 1) + (q1 - 1) * q2;
+      break;
+    case FLR_E_EDGES:
+      if (E->m < 0 || (E->m > 0 && !E->edges)) return FLR_EINVAL;
+      m = E->m;
+      break;
+    default: return FLR_EINVAL;
+  }
+  flr_handle* h = new (std::nothrow) flr_handle();
+  if (!h) return FLR_ENOMEM;
+  cudaGetDevice(&h->device);
+  cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->dtype = dtype;
+  h->n = n; h->p = p; h->m = m;
+  h->gkind = E->kind; h->q1 = q1; h->q2 = q2;
+  const size_t es = dtype_size(dtype);
+  const long long vec = 16 / (long long)es;
+  h->ldn = (n + vec - 1) / vec * vec;
+  flr_status s = FLR_OK;
+  auto fail = [&](flr_status st) { release(h); return st; };
+
+  // graph (validated on the host)
+  if (E->kind == FLR_E_EDGES) {
+    std::vector<int64_t> eh((size_t)(2 * m));
+    if (m > 0) {
+      if (mem == FLR_MEM_HOST) std::memcpy(eh.data(), E->edges, sizeof(int64_t) * 2 * m);
+      else if (cudaMemcpy(eh.data(), E->edges, sizeof(int64_t) * 2 * m, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(FLR_EINVAL);
+      }
+    }
+    if ((s = build_csr(h, eh.data(), m)) != FLR_OK) return fail(s);
+  }
+  // buffers
+  const size_t P = (size_t)p;
+  if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->Xt), (size_t)(p * h->ldn) * es)) != FLR_OK) return fail(s);
+  if ((s = dalloc(h, &h->y, (size_t)n)) != FLR_OK) return fail(s);
+  if ((s = dalloc(h, &h->c, P)) != FLR_OK) return fail(s);
+  if ((s = dalloc(h, &h->d, P)) != FLR_OK) return fail(s);
+  double** vecs[] = {&h->x, &h->r, &h->z, &h->pb0, &h->pb1, &h->q, &h->a, &h->wL, &h->wR,
+                     &h->wU, &h->wD, &h->idg, &h->binv};
+  for (double** v : vecs)
+    if ((s = dalloc(h, v, P)) != FLR_OK) return fail(s);
+  if ((s = dalloc(h, &h->K1, P * kMaxLevels)) != FLR_OK) return fail(s);
+  if ((s = dalloc(h, &h->K2, P * kMaxLevels)) != FLR_OK) return fail(s);
+  if (!h->wc && (s = dalloc(h, &h->wc, 1)) != FLR_OK) return fail(s);
+  const size_t accs = dtype == FLR_F64 ? 8 : 4;
+  if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->ub0), (size_t)h->ldn * accs)) != FLR_OK) return fail(s);
+  if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->ub1), (size_t)h->ldn * accs)) != FLR_OK) return fail(s);
+  if ((s = dalloc(h, &h->part, (size_t)2 * kNF * kMaxGrid)) != FLR_OK) return fail(s);
+  if ((s = dalloc(h, &h->ctl, 256)) != FLR_OK) return fail(s);
+  if (cudaMallocHost(&h->hctl, 256) != cudaSuccess) { (void)cudaGetLastError(); return fail(FLR_ENOMEM); }
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) return fail(FLR_ECUDA);
+
+  // X -> column-major copy (padding rows are zero), y, then X^T y and diag(X^T X)
+  if (cudaMemsetAsync(h->Xt, 0, (size_t)(p * h->ldn) * es, h->stream) != cudaSuccess) return fail(FLR_ECUDA);
+  const void* Xdev = X;
+  void* staging = nullptr;
+  if (mem == FLR_MEM_HOST) {
+    if (cudaMalloc(&staging, (size_t)(n * ldx) * es) != cudaSuccess) { (void)cudaGetLastError(); return fail(FLR_ENOMEM); }
+    if (cudaMemcpyAsync(staging, X, (size_t)(n * ldx) * es, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
+      cudaFree(staging);
+      return fail(FLR_ECUDA);
+    }
+    Xdev = staging;
+  }
+  if (cudaMemcpyAsync(h->y, y, sizeof(double) * n,
+                      mem == FLR_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                      h->stream) != cudaSuccess) {
+    if (staging) cudaFree(staging);
+    return fail(FLR_ECUDA);
+  }
+  switch (dtype) {
+    case FLR_F64: launch_setup<double>(h, Xdev, ldx); break;
+    case FLR_F32: launch_setup<float>(h, Xdev, ldx); break;
+    case FLR_BF16: launch_setup<__nv_bfloat16>(h, Xdev, ldx); break;
+    case FLR_F16: launch_setup<__half>(h, Xdev, ldx); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (staging) cudaFree(staging);
+  if (e != cudaSuccess) return fail(cuda_status(e));
+  std::vector<double> ch((size_t)p);
+  if (cudaMemcpy(ch.data(), h->c, sizeof(double) * p, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(FLR_ECUDA);
+  double s2 = 0.0;
+  for (double v : ch) s2 += v * v;
+  h->cnorm = std::sqrt(s2);
+  if (!std::isfinite(h->cnorm)) return fail(FLR_ENONFINITE);
+  *out = h;
+  return FLR_OK;
+}
+
+flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double tol,
+                     const flr_opts* opts, const double* beta_init, double* beta_out,
+                     int32_t io_mem, flr_stats* stats) {
+  if (!h || !beta_out) return FLR_EINVAL;
+  if (!(lambda1 >= 0.0) || !(lambda2 >= 0.0) || !(eps > 0.0) || !(tol > 0.0)) return FLR_EINVAL;
+  if (!std::isfinite(lambda1) || !std::isfinite(lambda2) || !std::isfinite(eps)) return FLR_EINVAL;
+  if (io_mem != FLR_MEM_DEVICE && io_mem != FLR_MEM_HOST) return FLR_EINVAL;
+  flr_opts o;
+  flr_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0)
+    return FLR_EINVAL;
+  int prev_dev = 0;
+  cudaGetDevice(&prev_dev);
+  if (prev_dev != h->device) cudaSetDevice(h->device);
+
+  int precond = o.precond;
+  if (precond == FLR_PC_AUTO) precond = h->gkind == FLR_E_CHAIN ? FLR_PC_TRIDIAG : FLR_PC_JACOBI;
+  if (precond != FLR_PC_JACOBI && precond != FLR_PC_TRIDIAG && precond != FLR_PC_PAPER) return FLR_EINVAL;
+  if (precond != FLR_PC_JACOBI && h->gkind == FLR_E_EDGES) return FLR_ENOTIMPL;
+
+  // grid: one block per SM at most; fewer for small problems
+  const long long work = h->n * h->p;
+  const long long per_block = h->dtype == FLR_F64 ? 8192 : 65536;
+  long long G = o.grid > 0 ? o.grid : (work + per_block - 1) / per_block;
+  G = std::max<long long>(1, std::min<long long>({G, (long long)h->sm_count, (long long)kMaxGrid, h->p}));
+  long long w = (h->p + G - 1) / G;
+  G = (h->p + w - 1) / w;
+  if (w > 8192) return FLR_ENOTIMPL;
+  int levels = 0;
+  while ((1LL << levels) < w) ++levels;
+  const long long wpad = (w + 3) / 4 * 4;
+  const int V = (int)(16 / dtype_size(h->dtype));
+  const size_t accs = h->dtype == FLR_F64 ? 8 : 4;
+  const size_t smem = (size_t)h->ldn * accs + (size_t)wpad * accs + (size_t)kThreads * V * accs +
+                      (size_t)wpad * 8 + 6 * (size_t)wpad * 8 + (size_t)(kWarps * kNF + kNF) * 8;
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
+
+  unsigned* bar = reinterpret_cast<unsigned*>(h->ctl);
+  int* err = reinterpret_cast<int*>(h->ctl + 64);
+  DevStats* dst = reinterpret_cast<DevStats*>(h->ctl + 128);
+  FLR_TRY(cudaMemsetAsync(h->ctl, 0, 128, h->stream));
+  FLR_TRY(cudaMemsetAsync(h->ctl + 128, 0xff, 128, h->stream));   // status -1 until written
+  const size_t accsz = (size_t)h->ldn * accs;
+  FLR_TRY(cudaMemsetAsync(h->ub0, 0, accsz, h->stream));
+  FLR_TRY(cudaMemsetAsync(h->ub1, 0, accsz, h->stream));
+  const double* binit = nullptr;
+  if (beta_init) {
+    FLR_TRY(cudaMemcpyAsync(h->x, beta_init, sizeof(double) * h->p,
+                            io_mem == FLR_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                            h->stream));
+    binit = h->x;
+  }
+
+  SolveParams P{};
+  P.Xt = h->Xt; P.n = h->n; P.p = h->p; P.ldn = h->ldn;
+  P.y = h->y; P.c = h->c; P.d = h->d; P.cnorm = h->cnorm > 0 ? h->cnorm : 1.0;
+  P.q2 = h->gkind == FLR_E_LATTICE ? h->q2 : h->p;
+  P.rowptr = h->rowptr; P.col = h->col;
+  P.lam1 = lambda1; P.lam2 = lambda2; P.eps = eps; P.tol = tol;
+  P.tol_cg = o.tol_cg > 0.0 ? o.tol_cg : tol;
+  P.max_mm = o.max_mm; P.max_cg = o.max_cg; P.min_cg = o.min_cg; P.precond = precond;
+  P.w = w; P.wpad = wpad; P.levels = levels;
+  P.beta_init = binit;
+  P.x = h->x; P.r = h->r; P.z = h->z; P.pb0 = h->pb0; P.pb1 = h->pb1; P.q = h->q; P.a = h->a;
+  P.wL = h->wL; P.wR = h->wR; P.wU = h->wU; P.wD = h->wD; P.wc = h->wc; P.idg = h->idg;
+  P.K1 = h->K1; P.K2 = h->K2; P.binv = h->binv;
+  P.ub0 = h->ub0; P.ub1 = h->ub1; P.part = h->part;
+  P.bar = bar; P.err = err; P.stats = dst;
+  P.timeout = o.wait_cycles > 0 ? o.wait_cycles : (1LL << 33);   // ~4 s of SM clock
+  P.inject_stall = o.inject_stall;
+
+  FLR_TRY(cudaEventRecord(h->ev0, h->stream));
+  flr_status ls = launch_solve(h, P, (int)G, smem);
+  if (ls != FLR_OK) return ls;
+  FLR_TRY(cudaEventRecord(h->ev1, h->stream));
+  FLR_TRY(cudaMemcpyAsync(h->hctl, h->ctl, 256, cudaMemcpyDeviceToHost, h->stream));
+  FLR_TRY(cudaMemcpyAsync(beta_out, h->x, sizeof(double) * h->p,
+                          io_mem == FLR_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          h->stream));
+  FLR_TRY(cudaStreamSynchronize(h->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  const int herr = *reinterpret_cast<const int*>(h->hctl + 64);
+  const DevStats* hs = reinterpret_cast<const DevStats*>(h->hctl + 128);
+  flr_status st = herr != DERR_NONE ? FLR_ETIMEOUT
+                  : hs->status == -1 ? FLR_ECUDA            // the kernel did not finish its work
+                                     : (flr_status)hs->status;
+  if (stats) {
+    stats->mm_iters = hs->mm_iters;
+    stats->cg_iters = hs->cg_iters;
+    stats->status = st;
+    stats->grid = (int)G;
+    stats->f = hs->f;
+    stats->f_eps = hs->f_eps;
+    stats->rel_change = hs->rel_change;
+    stats->cg_relres = hs->cg_relres;
+    stats->ms = ms;
+  }
+  if (prev_dev != h->device) cudaSetDevice(prev_dev);
+  return st;
+}
+
+flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const double* lambda2,
+                           double eps, double tol, const flr_opts* opts, double* betas,
+                           int32_t io_mem, double* objectives, flr_stats* stats) {
+  if (!h || K < 0 || (K > 0 && (!lambda1 || !lambda2 || !betas))) return FLR_EINVAL;
+  flr_status first = FLR_OK;
+  for (int k = 0; k < K; ++k) {
+    flr_stats st{};
+    flr_status s = flr_solve(h, lambda1[k], lambda2[k], eps, tol, opts, nullptr,
+                             betas + (size_t)k * h->p, io_mem, &st);
+    if (objectives) objectives[k] = st.f;
+    if (stats) stats[k] = st;
+    if (s != FLR_OK && first == FLR_OK) first = s;
+    if (s == FLR_EINVAL || s == FLR_ECUDA || s == FLR_ENOMEM) return s;
+  }
+  return first;
+}
+
+void flr_destroy(flr_t h) { release(h); }
+
+flr_status flr_get_info(flr_t h, int64_t* n, int64_t* p, int64_t* m, int32_t* dtype) {
+  if (!h) return FLR_EINVAL;
+  if (n) *n = h->n;
+  if (p) *p = h->p;
+  if (m) *m = h->m;
+  if (dtype) *dtype = h->dtype;
+  return FLR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// Device-side building blocks of the FLR solver: X-element traits, streaming
+// loads, a bounded grid barrier, deterministic block reductions.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace flr {
+
+constexpr int kThreads = 512;            // threads per block of the solve kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kNF = 4;                   // scalar fields per grid-reduction slot
+constexpr int kMaxLevels = 13;           // PCR levels: block chunks up to 8192 indices
+
+enum DevErr : int { DERR_NONE = 0, DERR_TIMEOUT = 1 };
+
+// ---------------------------------------------------------------------------
+// X element traits: V elements per 16-byte vector, accumulator type Acc.
+// ---------------------------------------------------------------------------
+template <typename TX> struct XT;
+
+__device__ __forceinline__ uint4 ld_stream16(const void* p) {
+  uint4 r;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+  return r;
+}
+
+template <> struct XT<double> {
+  static constexpr int V = 2;
+  using Acc = double;
+  __device__ static __forceinline__ void cvt(const uint4& v, double (&o)[2]) {
+    o[0] = __hiloint2double((int)v.y, (int)v.x);
+    o[1] = __hiloint2double((int)v.w, (int)v.z);
+  }
+};
+template <> struct XT<float> {
+  static constexpr int V = 4;
+  using Acc = float;
+  __device__ static __forceinline__ void cvt(const uint4& v, float (&o)[4]) {
+    o[0] = __uint_as_float(v.x); o[1] = __uint_as_float(v.y);
+    o[2] = __uint_as_float(v.z); o[3] = __uint_as_float(v.w);
+  }
+};
+template <> struct XT<__nv_bfloat16> {
+  static constexpr int V = 8;
+  using Acc = float;
+  __device__ static __forceinline__ void cvt(const uint4& v, float (&o)[8]) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {  // bf16 -> f32 is a 16-bit shift, exact
+      o[2 * i] = __uint_as_float(w[i] << 16);
+      o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+  }
+};
+template <> struct XT<__half> {
+  static constexpr int V = 8;
+  using Acc = float;
+  __device__ static __forceinline__ void cvt(const uint4& v, float (&o)[8]) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2 h = *reinterpret_cast<const __half2*>(&w[i]);
+      float2 f = __half22float2(h);
+      o[2 * i] = f.x;
+      o[2 * i + 1] = f.y;
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// coherent (L2) loads for data other blocks wrote during this launch
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
+
+// ---------------------------------------------------------------------------
+// Grid barrier for a cooperative launch.  `counter` is zeroed by the host
+// before the launch; barrier number e (1-based) completes when the counter
+// reaches e * gridDim.x.  Every wait is bounded: after `timeout` clock
+// cycles the block records DERR_TIMEOUT in *err and returns false, and a
+// block that sees *err set returns false too, so all blocks leave.
+// ---------------------------------------------------------------------------
+struct GridBarrier {
+  unsigned* counter;
+  int* err;
+  unsigned epoch;
+  long long timeout;
+
+  __device__ __forceinline__ bool sync() {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      epoch += 1;
+      const unsigned target = epoch * gridDim.x;
+      __threadfence();
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
+      int ok = 1;
+      const long long t0 = clock64();
+      unsigned spins = 0;
+      while (true) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+        if ((int)(v - target) >= 0) break;
+        if (*((volatile int*)err) != DERR_NONE) { ok = 0; break; }
+        if (++spins > 32) {
+          __nanosleep(32);
+          if (clock64() - t0 > timeout) {
+            atomicCAS(err, DERR_NONE, DERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+      s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions (fixed shuffle pattern, fixed warp order).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum NF doubles over the first `nw` warps of the block (warps >= nw must
+// pass zeros or not hold data); every thread returns the totals.
+// `rs` is kWarps*NF + NF doubles of shared memory.
+template <int NF>
+__device__ __forceinline__ void block_sum(double (&v)[NF], double* rs, int nw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < nw) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) v[f] = warp_sum(v[f]);
+    if (lane == 0) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) rs[warp * NF + f] = v[f];
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      double s = lane < nw ? rs[lane * NF + f] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) rs[kWarps * NF + f] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int f = 0; f < NF; ++f) v[f] = rs[kWarps * NF + f];
+  __syncthreads();
+}
+
+}  // namespace flr

@@ -1,0 +1,89 @@
+"""Write the oracle's reference solutions used by the parity tests and bench.py.
+
+Calls only oracle/ and flr_inputs/.  Each case is written to
+tests/golden/<name>.json:  the converged MM objective f and f_eps, the
+iteration count, the final relative change, input fingerprints (so a changed
+generator is caught before a parity comparison) and beta (all of it for
+p <= 4096, otherwise 512 sampled indices plus max |beta|).
+
+usage: python tests/golden/make_golden.py [case ...]     (default: the quick cases)
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import flr_inputs as fi  # noqa: E402
+from oracle import mm  # noqa: E402
+
+
+def fingerprint(pr):
+    X = pr.X64()
+    return {"x_sum": float(X.sum()), "x_sq": float((X * X).sum()),
+            "y_head": [float(v) for v in pr.y[:4]], "y_sum": float(pr.y.sum())}
+
+
+def cases():
+    """name -> (builder, solver, lam pairs or None)."""
+    return {
+        "config1": (lambda: fi.config(1), "dense", None),
+        "config2_q20": (lambda: fi.config(2, scale=0.04), "dense", None),
+        "config2_q40": (lambda: fi.config(2, scale=0.16), "woodbury", None),
+        "config4_small": (lambda: fi.config(4, scale=0.004), "dense", None),
+        "config3_small": (lambda: fi.config(3, scale=0.02), "dense", "grid"),
+        "paper_c1_p200": (lambda: fi.paper_scenario(1, 200, eps=1e-6), "dense", None),
+        "config2": (lambda: fi.config(2), "woodbury", None),
+    }
+
+
+QUICK = ["config1", "config2_q20", "config4_small", "config3_small", "paper_c1_p200",
+         "config2_q40"]
+
+
+def solve(pr, solver, lam1, lam2, log=None):
+    X = pr.X64()
+    E = pr.graph.edges
+    f = mm.mm_dense if solver == "dense" else mm.mm_woodbury
+    t = time.time()
+    r = f(X, pr.y, E, lam1, lam2, pr.eps, tol=1e-13, max_iter=12000)
+    out = {"lam1": lam1, "lam2": lam2, "f": r.f, "f_eps": r.f_eps, "iters": r.iters,
+           "rel_change": r.rel_change, "seconds": time.time() - t,
+           "f_trace_head": [float(v) for v in r.f_trace[:3]]}
+    b = r.beta
+    out["beta_absmax"] = float(np.abs(b).max())
+    if b.shape[0] <= 4096:
+        out["beta"] = [float(v) for v in b]
+    else:
+        idx = np.sort(np.random.default_rng(0).choice(b.shape[0], 512, replace=False))
+        out["beta_idx"] = [int(i) for i in idx]
+        out["beta_sample"] = [float(b[i]) for i in idx]
+    if log:
+        print(f"  lam=({lam1:g},{lam2:g}) iters={r.iters} f={r.f:.15g} {out['seconds']:.1f}s",
+              file=log, flush=True)
+    return out
+
+
+def make(name):
+    build, solver, lam = cases()[name]
+    pr = build()
+    rec = {"name": name, "problem": pr.name, "n": pr.n, "p": pr.p, "dtype": pr.dtype,
+           "graph": pr.graph.kind, "q1": pr.graph.q1, "q2": pr.graph.q2, "eps": pr.eps,
+           "solver": solver, "fingerprint": fingerprint(pr)}
+    print(name, pr.name, flush=True)
+    if lam == "grid":
+        rec["solutions"] = [solve(pr, solver, float(l1), float(l2), sys.stdout)
+                            for l1, l2 in pr.lam_grid]
+    else:
+        rec.update(solve(pr, solver, pr.lam1, pr.lam2, sys.stdout))
+    with open(os.path.join(HERE, name + ".json"), "w") as fh:
+        json.dump(rec, fh, indent=1)
+
+
+if __name__ == "__main__":
+    for nm in (sys.argv[1:] or QUICK):
+        make(nm)

@@ -1,0 +1,316 @@
+"""GPU parity: the CUDA MM/PCG solve (through the C ABI) against the FP64 oracle.
+
+Parity bar: relative objective gap |f_gpu - f_oracle| / f_oracle <= 1e-6, and,
+when both sides run the MM to a tight stop, max |beta_gpu - beta_oracle| <=
+1e-4 max |beta_oracle|.  Oracle values come from tests/golden/*.json (written
+by tests/golden/make_golden.py, which calls only oracle/) or from running the
+oracle inline on small cases.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import flr_inputs as fi
+from oracle import exact, mm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+GAP = 1e-6
+BETA = 1e-4
+
+
+@pytest.fixture(scope="module")
+def flr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1306_1970_gb300 as m
+    m.load(build_if_missing=True)
+    return m
+
+
+def golden(name):
+    path = os.path.join(GOLD, name + ".json")
+    if not os.path.exists(path):
+        pytest.skip(f"golden {name} not generated")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def check_fingerprint(pr, g):
+    X = pr.X64()
+    fp = g["fingerprint"]
+    assert abs(X.sum() - fp["x_sum"]) <= 1e-6 * max(1.0, abs(fp["x_sum"])) + 1e-6
+    np.testing.assert_allclose(pr.y[:4], fp["y_head"], rtol=1e-12, atol=1e-12)
+
+
+def problem(flr, pr, host=False, graph=None):
+    X = torch.from_numpy(np.ascontiguousarray(pr.X))
+    if pr.dtype == "bf16":
+        X = X.view(torch.int16)
+    y = torch.from_numpy(pr.y)
+    if not host:
+        X, y = X.cuda(), y.cuda()
+    else:
+        X, y = X.pin_memory(), y.pin_memory()
+    dt = pr.dtype if pr.dtype in ("bf16",) else None
+    return flr.Problem(X, y, graph or pr.graph, dtype=dt)
+
+
+def assert_parity(st, beta, f_ref, beta_ref, check_beta=True):
+    gap = abs(st.f - f_ref) / abs(f_ref)
+    assert st.status == 0, st
+    assert gap <= GAP, (gap, st)
+    if check_beta:
+        b = beta.cpu().numpy() if hasattr(beta, "cpu") else beta
+        db = np.abs(b - beta_ref).max() / np.abs(beta_ref).max()
+        assert db <= BETA, (db, st)
+
+
+# --------------------------------------------------------------------------- configurations
+@pytest.mark.parametrize("precond", ["tridiag", "jacobi", "paper"])
+def test_config1_chain_f64(flr, precond):
+    g = golden("config1")
+    pr = fi.config(1)
+    check_fingerprint(pr, g)
+    prob = problem(flr, pr)
+    beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-12, precond=precond,
+                          max_mm=20000, tol_cg=1e-12)
+    assert_parity(st, beta, g["f"], np.array(g["beta"]))
+
+
+@pytest.mark.parametrize("grid", [1, 2, 3, 7, 13])
+def test_config1_grid_shapes(flr, grid):
+    """Several block counts (ragged last block) give the oracle's answer."""
+    g = golden("config1")
+    pr = fi.config(1)
+    prob = problem(flr, pr)
+    beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-12, grid=grid, max_mm=20000,
+                          tol_cg=1e-12)
+    assert st.grid == grid
+    assert_parity(st, beta, g["f"], np.array(g["beta"]))
+
+
+def test_config2_lattice_f32_small(flr):
+    g = golden("config2_q20")
+    pr = fi.config(2, scale=0.04)
+    check_fingerprint(pr, g)
+    prob = problem(flr, pr)
+    beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-13, max_mm=20000, tol_cg=1e-10)
+    assert_parity(st, beta, g["f"], np.array(g["beta"]))
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "tridiag"])
+def test_config2_lattice_q40(flr, precond):
+    g = golden("config2_q40")
+    pr = fi.config(2, scale=0.16)
+    check_fingerprint(pr, g)
+    prob = problem(flr, pr)
+    beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-9, precond=precond,
+                          tol_cg=1e-8, max_mm=20000)
+    assert_parity(st, beta, g["f"], np.array(g["beta"]), check_beta=False)
+
+
+def test_config4_lattice_f16_small(flr):
+    g = golden("config4_small")
+    pr = fi.config(4, scale=0.004)
+    check_fingerprint(pr, g)
+    prob = problem(flr, pr)
+    beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-13, max_mm=20000, tol_cg=1e-10)
+    assert_parity(st, beta, g["f"], np.array(g["beta"]))
+
+
+def test_bf16_chain_against_inline_oracle(flr):
+    pr = fi.config(3, scale=0.01)        # n=20, p=200, BF16 X
+    lam1, lam2 = 0.1, 0.3
+    ref = mm.mm_dense(pr.X64(), pr.y, pr.graph.edges, lam1, lam2, pr.eps, tol=1e-13)
+    prob = problem(flr, pr)
+    beta, st = prob.solve(lam1, lam2, eps=pr.eps, tol=1e-13, max_mm=20000, tol_cg=1e-10)
+    assert_parity(st, beta, ref.f, ref.beta)
+
+
+def test_config2_full_size(flr):
+    """The bench workload (q=100 lattice, n=1000, FP32) against the stored oracle solve."""
+    g = golden("config2")
+    pr = fi.config(2)
+    check_fingerprint(pr, g)
+    prob = problem(flr, pr)
+    beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-9, tol_cg=1e-8, max_mm=20000)
+    gap = abs(st.f - g["f"]) / g["f"]
+    assert st.status == 0 and gap <= GAP, (gap, st)
+    b = beta.cpu().numpy()
+    idx = np.array(g["beta_idx"])
+    db = np.abs(b[idx] - np.array(g["beta_sample"])).max() / g["beta_absmax"]
+    assert db <= 1e-2, db
+
+
+# --------------------------------------------------------------------------- special cases
+def test_identity_no_fusion_is_soft_threshold(flr):
+    rng = np.random.default_rng(20)
+    p = 96
+    y = rng.standard_normal(p) * 2
+    X = torch.eye(p, dtype=torch.float64).cuda()
+    prob = flr.Problem(X, torch.from_numpy(y).cuda(), {"kind": "chain"})
+    beta, st = prob.solve(0.6, 0.0, eps=1e-9, tol=1e-15, max_mm=5000, tol_cg=1e-14)
+    np.testing.assert_allclose(beta.cpu().numpy(), exact.soft_threshold(y, 0.6), atol=1e-6)
+
+
+def test_identity_chain_is_exact_flsa(flr):
+    rng = np.random.default_rng(21)
+    p = 120
+    y = np.repeat(rng.standard_normal(8) * 2, 15) + 0.3 * rng.standard_normal(p)
+    lam1, lam2, eps = 0.2, 0.7, 1e-7
+    E = fi.chain_edges(p)
+    b_star = exact.flsa_chain(y, lam1, lam2)
+    f_star = mm.objective(np.eye(p), y, b_star, lam1, lam2, E)
+    X = torch.eye(p, dtype=torch.float64).cuda()
+    prob = flr.Problem(X, torch.from_numpy(y).cuda(), {"kind": "chain"})
+    beta, st = prob.solve(lam1, lam2, eps=eps, tol=1e-15, max_mm=50000, tol_cg=1e-14)
+    b = beta.cpu().numpy()
+    slack = mm.eps_gap(b, lam1, lam2, E, eps)
+    assert f_star - 1e-9 <= st.f <= f_star + slack + 1e-8 * f_star
+    assert np.abs(b - b_star).max() < 1e-3
+
+
+def test_unpenalised_is_least_squares(flr):
+    rng = np.random.default_rng(22)
+    X = rng.standard_normal((200, 30))
+    y = rng.standard_normal(200)
+    prob = flr.Problem(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), {"kind": "chain"})
+    beta, st = prob.solve(0.0, 0.0, eps=1e-6, tol=1e-14, max_mm=3, tol_cg=1e-14, precond="jacobi")
+    np.testing.assert_allclose(beta.cpu().numpy(), exact.least_squares(X, y), rtol=1e-8, atol=1e-10)
+
+
+def test_edge_list_matches_stencil(flr):
+    """The same lattice as an explicit edge list (CSR path) and as a stencil."""
+    pr = fi.config(2, scale=0.04)
+    a = problem(flr, pr)
+    b = problem(flr, pr, graph={"kind": "edges", "edges": pr.graph.edges})
+    kw = dict(eps=pr.eps, tol=1e-10, tol_cg=1e-10, precond="jacobi", max_mm=20000)
+    ba, sa = a.solve(pr.lam1, pr.lam2, **kw)
+    bb, sb = b.solve(pr.lam1, pr.lam2, **kw)
+    assert abs(sa.f - sb.f) <= 1e-9 * sa.f
+    assert (ba - bb).abs().max().item() <= 1e-6 * ba.abs().max().item()
+
+
+def test_knn_graph_against_oracle(flr):
+    rng = np.random.default_rng(23)
+    p, n = 150, 60
+    pts = rng.uniform(size=(p, 2))
+    E = fi.knn_edges(pts, 5)
+    beta_t = np.where(pts[:, 0] < 0.3, 1.0, np.where(pts[:, 0] > 0.7, -1.0, 0.0))
+    X = rng.standard_normal((n, p)).astype(np.float32)
+    y = X.astype(np.float64) @ beta_t + rng.standard_normal(n)
+    ref = mm.mm_dense(X.astype(np.float64), y, E, 0.1, 0.3, 1e-6, tol=1e-13)
+    prob = flr.Problem(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(),
+                       {"kind": "edges", "edges": E})
+    beta, st = prob.solve(0.1, 0.3, eps=1e-6, tol=1e-13, max_mm=20000, tol_cg=1e-10)
+    assert_parity(st, beta, ref.f, ref.beta)
+
+
+# --------------------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("n,p,dtype", [(1, 1, "f64"), (1, 5, "f32"), (37, 23, "f32"),
+                                       (9, 41, "f16"), (130, 3, "f64")])
+def test_tiny_and_ragged_shapes(flr, n, p, dtype):
+    rng = np.random.default_rng(n * 100 + p)
+    Xd = rng.standard_normal((n, p))
+    Xs, Xw = fi.quantize(Xd, dtype)
+    y = Xw @ np.linspace(-1, 1, p) + 0.1 * rng.standard_normal(n)
+    E = fi.chain_edges(p)
+    ref = mm.mm_dense(Xw, y, E, 0.2, 0.4, 1e-6, tol=1e-13)
+    prob = flr.Problem(torch.from_numpy(np.ascontiguousarray(Xs)).cuda(),
+                       torch.from_numpy(y).cuda(), {"kind": "chain"})
+    beta, st = prob.solve(0.2, 0.4, eps=1e-6, tol=1e-13, max_mm=20000, tol_cg=1e-11)
+    assert_parity(st, beta, ref.f, ref.beta)
+
+
+def test_empty_edge_set_and_zero_column(flr):
+    rng = np.random.default_rng(24)
+    X = rng.standard_normal((40, 12))
+    X[:, 5] = 0.0
+    y = rng.standard_normal(40)
+    E = np.zeros((0, 2), np.int64)
+    ref = mm.mm_dense(X, y, E, 0.3, 0.5, 1e-6, tol=1e-13)
+    prob = flr.Problem(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(),
+                       {"kind": "edges", "edges": E})
+    beta, st = prob.solve(0.3, 0.5, eps=1e-6, tol=1e-13, max_mm=20000, tol_cg=1e-12)
+    assert_parity(st, beta, ref.f, ref.beta)
+    assert beta[5].item() == 0.0
+
+
+def test_host_buffers_match_device(flr):
+    pr = fi.config(1)
+    a = problem(flr, pr)
+    b = problem(flr, pr, host=True)
+    ba, sa = a.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-10)
+    out = torch.empty(pr.p, dtype=torch.float64).pin_memory()
+    bb, sb = b.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-10, out=out)
+    assert sa.f == sb.f
+    assert torch.equal(ba.cpu(), bb)
+
+
+def test_repeat_is_deterministic(flr):
+    pr = fi.config(2, scale=0.04)
+    prob = problem(flr, pr)
+    b1, s1 = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-8)
+    b2, s2 = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-8)
+    assert s1.mm_iters == s2.mm_iters
+    assert abs(s1.f - s2.f) <= 1e-12 * abs(s1.f)
+
+
+def test_notconv_and_warm_start(flr):
+    g = golden("config1")
+    pr = fi.config(1)
+    prob = problem(flr, pr)
+    _, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-12, max_mm=3)
+    assert st.status == flr.FLR_ENOTCONV and st.mm_iters == 3
+    b0 = torch.tensor(g["beta"], dtype=torch.float64).cuda()
+    beta, st2 = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-9, beta_init=b0)
+    assert st2.mm_iters <= 3
+    assert abs(st2.f - g["f"]) <= 1e-8 * g["f"]
+
+
+def test_batch_equals_single(flr):
+    pr = fi.config(1, scale=0.5)
+    prob = problem(flr, pr)
+    l1, l2 = [0.05, 0.1, 0.3], [0.2, 0.5, 0.1]
+    betas, objs, sts = prob.solve_batch(l1, l2, eps=pr.eps, tol=1e-10)
+    for k in range(3):
+        b, s = prob.solve(l1[k], l2[k], eps=pr.eps, tol=1e-10)
+        assert objs[k] == s.f
+        assert torch.equal(betas[:, k], b)
+
+
+@pytest.mark.parametrize("bad", ["self_loop", "duplicate", "reversed_duplicate", "out_of_range"])
+def test_invalid_edges_rejected(flr, bad):
+    X = torch.randn(10, 6, dtype=torch.float64).cuda()
+    y = torch.randn(10, dtype=torch.float64).cuda()
+    E = {"self_loop": [[0, 1], [2, 2]], "duplicate": [[0, 1], [0, 1]],
+         "reversed_duplicate": [[0, 1], [1, 0]], "out_of_range": [[0, 6]]}[bad]
+    with pytest.raises(flr.FlrError) as ei:
+        flr.Problem(X, y, {"kind": "edges", "edges": np.array(E)})
+    assert ei.value.status == flr.FLR_EINVAL
+
+
+def test_invalid_solve_arguments(flr):
+    prob = problem(flr, fi.config(1, scale=0.3))
+    for args in [(-1.0, 0.1, 1e-6, 1e-8), (0.1, 0.1, 0.0, 1e-8), (0.1, 0.1, 1e-6, 0.0),
+                 (float("nan"), 0.1, 1e-6, 1e-8)]:
+        with pytest.raises(flr.FlrError) as ei:
+            prob.solve(*args[:2], eps=args[2], tol=args[3])
+        assert ei.value.status == flr.FLR_EINVAL
+
+
+def test_bounded_wait_expires_without_fault(flr):
+    """Block 0 skips the first grid barrier: the others' waits time out and the
+    solve reports FLR_ETIMEOUT; the context stays usable for the next solve."""
+    pr = fi.config(1)
+    prob = problem(flr, pr)
+    _, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-8, grid=4, inject_stall=1,
+                       wait_cycles=50_000_000, check=False)
+    assert st.status == flr.FLR_ETIMEOUT
+    beta, st2 = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-8)
+    assert st2.status == 0 and np.isfinite(st2.f)
