@@ -317,9 +317,9 @@ flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_
   if ((s = dalloc(h, &h->K1, P * kMaxLevels)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, &h->K2, P * kMaxLevels)) != FLR_OK) return fail(s);
   if (!h->wc && (s = dalloc(h, &h->wc, 1)) != FLR_OK) return fail(s);
-  const size_t accs = dtype == FLR_F64 ? 8 : 4;
-  if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->ub0), (size_t)h->ldn * accs)) != FLR_OK) return fail(s);
-  if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->ub1), (size_t)h->ldn * accs)) != FLR_OK) return fail(s);
+  // u buffers hold doubles (the FP64 refinement pass) and floats (FP32 CG products)
+  if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->ub0), (size_t)h->ldn * 8)) != FLR_OK) return fail(s);
+  if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->ub1), (size_t)h->ldn * 8)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, &h->part, (size_t)2 * kNF * kMaxGrid)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, &h->ctl, 256)) != FLR_OK) return fail(s);
   if (cudaMallocHost(&h->hctl, 256) != cudaSuccess) { (void)cudaGetLastError(); return fail(FLR_ENOMEM); }
@@ -396,9 +396,7 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   while ((1LL << levels) < w) ++levels;
   const long long wpad = (w + 3) / 4 * 4;
   const int V = (int)(16 / dtype_size(h->dtype));
-  const size_t accs = h->dtype == FLR_F64 ? 8 : 4;
-  const size_t smem = (size_t)h->ldn * accs + (size_t)wpad * accs + (size_t)kThreads * V * accs +
-                      (size_t)wpad * 8 + 6 * (size_t)wpad * 8 + (size_t)(kWarps * kNF + kNF) * 8;
+  const size_t smem = solve_smem_bytes(h->ldn, wpad, V);
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
@@ -408,7 +406,7 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   DevStats* dst = reinterpret_cast<DevStats*>(h->ctl + 128);
   FLR_TRY(cudaMemsetAsync(h->ctl, 0, 128, h->stream));
   FLR_TRY(cudaMemsetAsync(h->ctl + 128, 0xff, 128, h->stream));   // status -1 until written
-  const size_t accsz = (size_t)h->ldn * accs;
+  const size_t accsz = (size_t)h->ldn * 8;
   FLR_TRY(cudaMemsetAsync(h->ub0, 0, accsz, h->stream));
   FLR_TRY(cudaMemsetAsync(h->ub1, 0, accsz, h->stream));
   const double* binit = nullptr;

@@ -9,8 +9,16 @@
 //
 // Work decomposition: block b owns the contiguous coefficient range
 // [j0, j1) and the matching column slab of X, stored column-major (Xt[j][i]
-// = X[i][j], row length ldn).  One CG iteration is
-//   phase A: u += X[:, j0:j1] p[j0:j1]   (FP32 or FP64 atomics into u)
+// = X[i][j], row length ldn).
+//
+// Once per MM iteration (refinement pass, FP64 accumulation over exactly
+// widened X): u0 = X b, f(b) from u0 (Eq. obj), r0 = c - X^T u0 - S b with
+// S = lam1 A + lam2 B.  This is the outer residual of a mixed-precision
+// iterative refinement: the inner CG below may use FP32 products, while
+// every MM iteration restarts from an FP64-accurate residual and objective.
+//
+// One CG iteration (products accumulate in FP32 for FP32/BF16/FP16 X):
+//   phase A: u += X[:, j0:j1] p[j0:j1]   (atomics into u)
 //            Sp_j = lam1 a_j p_j + lam2 sum_k w_jk (p_j - p_k) and p^T S p
 //   barrier 1
 //            p^T Q p = ||u||^2 + p^T S p;  nu = r^T z / p^T Q p
@@ -24,6 +32,9 @@
 // decisions.  Halo values of p (neighbours owned by other blocks) are
 // recomputed as z_k + gamma p_old_k from double-buffered p, bit-identical
 // to the owner's own update.
+//
+// FP64 arithmetic is scarce on this GPU, so scalar work runs in one thread
+// and block reductions go through shared memory and a single warp.
 #pragma once
 #include "flr_device.cuh"
 
@@ -39,6 +50,9 @@ enum GraphKind : int { GK_STENCIL = 0, GK_CSR = 1 };
 enum SolveStatus : int {
   ST_OK = 0, ST_NOTCONV = 4, ST_BREAKDOWN = 5, ST_NONFINITE = 6, ST_TIMEOUT = 7
 };
+enum NbrBits : unsigned char { NB_L = 1, NB_R = 2, NB_U = 4, NB_D = 8 };
+
+constexpr int kRF = 2;   // fields per block reduction
 
 struct SolveParams {
   const void* Xt;
@@ -57,7 +71,7 @@ struct SolveParams {
   const double* beta_init;   // nullptr -> X_j^T y / X_j^T X_j
   // state
   double *x, *r, *z, *pb0, *pb1, *q, *a, *wL, *wR, *wU, *wD, *wc, *idg, *K1, *K2, *binv;
-  void* ub0;
+  void* ub0;                 // two n-vectors of doubles (also used as floats)
   void* ub1;
   double* part;              // [2 slots][kNF][gridDim.x]
   unsigned* bar;
@@ -67,24 +81,60 @@ struct SolveParams {
   int inject_stall;          // test hook: block 0 skips the first barrier
 };
 
+// shared-memory bytes of mm_solve_kernel (the host uses the same formula)
+__host__ __device__ inline size_t solve_smem_bytes(long long ldn, long long wpad, int V) {
+  return (size_t)ldn * 8 + (size_t)wpad * 8 + (size_t)kThreads * V * 8 + (size_t)wpad * 8 +
+         6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 + ((size_t)kRF * kThreads + 16) * 8 +
+         (size_t)wpad;
+}
+
+template <typename TX, typename A>
+__device__ __forceinline__ void cvt_to(const uint4& raw, A (&o)[XT<TX>::V]) {
+  typename XT<TX>::Acc t[XT<TX>::V];
+  XT<TX>::cvt(raw, t);
+#pragma unroll
+  for (int e = 0; e < XT<TX>::V; ++e) o[e] = (A)t[e];
+}
+
+// Block sum of F per-thread doubles; threads >= nact must hold zeros.
+// rs: kRF*kThreads + 16 doubles.  Every thread returns the totals.
+template <int F>
+__device__ __forceinline__ void block_reduce(double (&v)[F], double* rs, int nact) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = nact >= kThreads ? kWarps : (nact + 31) / 32;
+  if (warp < nw) {
+#pragma unroll
+    for (int f = 0; f < F; ++f) rs[f * kThreads + tid] = v[f];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      double s = 0.0;
+      for (int k = 0; k < nw; ++k) s += rs[f * kThreads + k * 32 + lane];
+      s = warp_sum(s);
+      if (lane == 0) rs[kRF * kThreads + f] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int f = 0; f < F; ++f) v[f] = rs[kRF * kThreads + f];
+}
+
 // u[0:n] += sum_{j in slab} X[:, j] * v[j - j0]   (v staged in shared memory)
-template <typename TX>
+template <typename TX, typename A>
 __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restrict__ Xt,
-                                        long long j0, int wl,
-                                        const typename XT<TX>::Acc* vs,
-                                        typename XT<TX>::Acc* red,
-                                        typename XT<TX>::Acc* u) {
-  using Acc = typename XT<TX>::Acc;
+                                        long long j0, int wl, const A* vs, A* red, A* u) {
   constexpr int V = XT<TX>::V;
   const int tid = threadIdx.x;
-  const long long nv = P.ldn / V;
+  const int nv = (int)(P.ldn / V);
   if (wl <= 0) return;
   if (nv >= kThreads) {
-    for (long long rv = tid; rv < nv; rv += kThreads) {
-      Acc acc[V];
+    for (int rv = tid; rv < nv; rv += kThreads) {
+      A acc[V];
 #pragma unroll
-      for (int e = 0; e < V; ++e) acc[e] = Acc(0);
-      const TX* base = Xt + j0 * P.ldn + rv * V;
+      for (int e = 0; e < V; ++e) acc[e] = A(0);
+      const TX* base = Xt + j0 * P.ldn + (long long)rv * V;
       int j = 0;
       for (; j + 4 <= wl; j += 4) {
         uint4 raw[4];
@@ -92,32 +142,32 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
         for (int k = 0; k < 4; ++k) raw[k] = ld_stream16(base + (long long)(j + k) * P.ldn);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          Acc xv[V];
-          XT<TX>::cvt(raw[k], xv);
-          const Acc s = vs[j + k];
+          A xv[V];
+          cvt_to<TX, A>(raw[k], xv);
+          const A s = vs[j + k];
 #pragma unroll
           for (int e = 0; e < V; ++e) acc[e] = fma(xv[e], s, acc[e]);
         }
       }
       for (; j < wl; ++j) {
-        Acc xv[V];
-        XT<TX>::cvt(ld_stream16(base + (long long)j * P.ldn), xv);
-        const Acc s = vs[j];
+        A xv[V];
+        cvt_to<TX, A>(ld_stream16(base + (long long)j * P.ldn), xv);
+        const A s = vs[j];
 #pragma unroll
         for (int e = 0; e < V; ++e) acc[e] = fma(xv[e], s, acc[e]);
       }
 #pragma unroll
       for (int e = 0; e < V; ++e) {
-        const long long i = rv * V + e;
-        if (i < P.n && acc[e] != Acc(0)) atomicAdd(u + i, acc[e]);
+        const long long i = (long long)rv * V + e;
+        if (i < P.n && acc[e] != A(0)) atomicAdd(u + i, acc[e]);
       }
     }
   } else {
-    const int ncg = kThreads / (int)nv;          // column groups, >= 1
-    const int rv = tid % (int)nv, cg = tid / (int)nv;
-    Acc acc[V];
+    const int ncg = kThreads / nv;          // column groups, >= 1
+    const int rv = tid % nv, cg = tid / nv;
+    A acc[V];
 #pragma unroll
-    for (int e = 0; e < V; ++e) acc[e] = Acc(0);
+    for (int e = 0; e < V; ++e) acc[e] = A(0);
     if (cg < ncg) {
       const TX* base = Xt + j0 * P.ldn + (long long)rv * V;
       int j = cg;
@@ -127,50 +177,48 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
         for (int k = 0; k < 4; ++k) raw[k] = ld_stream16(base + (long long)(j + k * ncg) * P.ldn);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          Acc xv[V];
-          XT<TX>::cvt(raw[k], xv);
-          const Acc s = vs[j + k * ncg];
+          A xv[V];
+          cvt_to<TX, A>(raw[k], xv);
+          const A s = vs[j + k * ncg];
 #pragma unroll
           for (int e = 0; e < V; ++e) acc[e] = fma(xv[e], s, acc[e]);
         }
       }
       for (; j < wl; j += ncg) {
-        Acc xv[V];
-        XT<TX>::cvt(ld_stream16(base + (long long)j * P.ldn), xv);
-        const Acc s = vs[j];
+        A xv[V];
+        cvt_to<TX, A>(ld_stream16(base + (long long)j * P.ldn), xv);
+        const A s = vs[j];
 #pragma unroll
         for (int e = 0; e < V; ++e) acc[e] = fma(xv[e], s, acc[e]);
       }
 #pragma unroll
-      for (int e = 0; e < V; ++e) red[(long long)cg * nv * V + (long long)rv * V + e] = acc[e];
+      for (int e = 0; e < V; ++e) red[cg * nv * V + rv * V + e] = acc[e];
     }
     __syncthreads();
-    const int rows = (int)nv * V;
+    const int rows = nv * V;
     for (int i = tid; i < rows; i += kThreads) {
-      Acc s = Acc(0);
+      A s = A(0);
       for (int g = 0; g < ncg; ++g) s += red[g * rows + i];
-      if (i < P.n && s != Acc(0)) atomicAdd(u + i, s);
+      if (i < P.n && s != A(0)) atomicAdd(u + i, s);
     }
     __syncthreads();
   }
 }
 
 // tv[jj] = X[:, j0+jj]^T u  for jj in [0, wl)   (u staged in shared memory)
-template <typename TX>
+template <typename TX, typename A>
 __device__ __forceinline__ void phase_c(const SolveParams& P, const TX* __restrict__ Xt,
-                                        long long j0, int wl,
-                                        const typename XT<TX>::Acc* us, double* tv) {
-  using Acc = typename XT<TX>::Acc;
+                                        long long j0, int wl, const A* us, double* tv) {
   constexpr int V = XT<TX>::V;
   constexpr int CPW = 4;  // columns per warp in flight
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nv = (int)(P.ldn / V);
   for (int base = warp * CPW; base < wl; base += kWarps * CPW) {
-    Acc acc[CPW];
+    A acc[CPW];
 #pragma unroll
-    for (int c = 0; c < CPW; ++c) acc[c] = Acc(0);
+    for (int c = 0; c < CPW; ++c) acc[c] = A(0);
     for (int rv = lane; rv < nv; rv += 32) {
-      Acc uu[V];
+      A uu[V];
 #pragma unroll
       for (int e = 0; e < V; ++e) uu[e] = us[rv * V + e];
       uint4 raw[CPW];
@@ -180,8 +228,8 @@ __device__ __forceinline__ void phase_c(const SolveParams& P, const TX* __restri
 #pragma unroll
       for (int c = 0; c < CPW; ++c) {
         if (base + c < wl) {
-          Acc xv[V];
-          XT<TX>::cvt(raw[c], xv);
+          A xv[V];
+          cvt_to<TX, A>(raw[c], xv);
 #pragma unroll
           for (int e = 0; e < V; ++e) acc[c] = fma(xv[e], uu[e], acc[c]);
         }
@@ -189,24 +237,64 @@ __device__ __forceinline__ void phase_c(const SolveParams& P, const TX* __restri
     }
 #pragma unroll
     for (int c = 0; c < CPW; ++c) {
-      const Acc s = warp_sum(acc[c]);
+      const A s = warp_sum(acc[c]);
       if (lane == 0 && base + c < wl) tv[base + c] = (double)s;
     }
   }
   __syncthreads();
 }
 
-// z[own] = M^-1 r[own].  Jacobi: r * idg.  Tridiagonal: parallel cyclic
-// reduction over the block's chunk with multipliers precomputed per MM
-// iteration (K1, K2, binv); `w0`/`w1` are two chunk-sized shared buffers.
-__device__ __forceinline__ void apply_precond(const SolveParams& P, long long j0, int wl,
-                                              double* w0, double* w1) {
+// Precompute the PCR multipliers of the chunk's tridiagonal matrix
+// (diagonal `diag`, couplings -lw / -rw between consecutive indices).
+__device__ __forceinline__ void setup_tridiag(const SolveParams& P, long long j0, int wl,
+                                              const double* diag, const double* lw,
+                                              const double* rw, double* sm6) {
   const int tid = threadIdx.x;
-  if (P.precond == PC_JACOBI) {
+  const long long wp = P.wpad;
+  double* A0 = sm6;          double* B0 = sm6 + wp;     double* C0 = sm6 + 2 * wp;
+  double* A1 = sm6 + 3 * wp; double* B1 = sm6 + 4 * wp; double* C1 = sm6 + 5 * wp;
+  for (int jj = tid; jj < wl; jj += kThreads) {
+    B0[jj] = diag[jj];
+    A0[jj] = jj > 0 ? -lw[jj] : 0.0;
+    C0[jj] = jj + 1 < wl ? -rw[jj] : 0.0;
+  }
+  __syncthreads();
+  double *A = A0, *B = B0, *C = C0, *An = A1, *Bn = B1, *Cn = C1;
+  for (int l = 0; l < P.levels; ++l) {
+    const int s = 1 << l;
     for (int jj = tid; jj < wl; jj += kThreads) {
       const long long j = j0 + jj;
-      P.z[j] = P.r[j] * P.idg[j];
+      double k1 = 0.0, k2 = 0.0, bb = B[jj], an = 0.0, cn = 0.0;
+      if (jj >= s) {
+        k1 = A[jj] / B[jj - s];
+        an = -A[jj - s] * k1;
+        bb = fma(-C[jj - s], k1, bb);
+      }
+      if (jj + s < wl) {
+        k2 = C[jj] / B[jj + s];
+        cn = -C[jj + s] * k2;
+        bb = fma(-A[jj + s], k2, bb);
+      }
+      P.K1[(long long)l * P.p + j] = k1;
+      P.K2[(long long)l * P.p + j] = k2;
+      An[jj] = an; Bn[jj] = bb; Cn[jj] = cn;
     }
+    __syncthreads();
+    double* t;
+    t = A; A = An; An = t;
+    t = B; B = Bn; Bn = t;
+    t = C; C = Cn; Cn = t;
+  }
+  for (int jj = tid; jj < wl; jj += kThreads) P.binv[j0 + jj] = 1.0 / B[jj];
+  __syncthreads();
+}
+
+// z[own] = M^-1 r[own] (Jacobi, or PCR with the precomputed multipliers)
+__device__ __forceinline__ void apply_precond(const SolveParams& P, long long j0, int wl,
+                                              const double* sidg, double* w0, double* w1) {
+  const int tid = threadIdx.x;
+  if (P.precond == PC_JACOBI) {
+    for (int jj = tid; jj < wl; jj += kThreads) P.z[j0 + jj] = P.r[j0 + jj] * sidg[jj];
     __syncthreads();
     return;
   }
@@ -230,56 +318,6 @@ __device__ __forceinline__ void apply_precond(const SolveParams& P, long long j0
   __syncthreads();
 }
 
-// Precompute the PCR multipliers of the chunk's tridiagonal matrix
-// (diag D, couplings -lam2 w between consecutive indices inside the chunk).
-__device__ __forceinline__ void setup_tridiag(const SolveParams& P, long long j0, int wl,
-                                              double* sm6) {
-  const int tid = threadIdx.x;
-  const long long wp = P.wpad;
-  double* A0 = sm6;          double* B0 = sm6 + wp;     double* C0 = sm6 + 2 * wp;
-  double* A1 = sm6 + 3 * wp; double* B1 = sm6 + 4 * wp; double* C1 = sm6 + 5 * wp;
-  for (int jj = tid; jj < wl; jj += kThreads) {
-    const long long j = j0 + jj;
-    double dj = P.lam1 * P.a[j];
-    // full weighted degree on the diagonal (all edges of j)
-    double deg = P.wL[j] + P.wR[j] + P.wU[j] + P.wD[j];
-    dj = fma(P.lam2, deg, dj);
-    if (P.precond == PC_TRIDIAG) dj += P.d[j];
-    B0[jj] = dj;
-    A0[jj] = jj > 0 ? -P.lam2 * P.wL[j] : 0.0;
-    C0[jj] = jj + 1 < wl ? -P.lam2 * P.wR[j] : 0.0;
-  }
-  __syncthreads();
-  double *A = A0, *B = B0, *C = C0, *An = A1, *Bn = B1, *Cn = C1;
-  for (int l = 0; l < P.levels; ++l) {
-    const int s = 1 << l;
-    for (int jj = tid; jj < wl; jj += kThreads) {
-      const long long j = j0 + jj;
-      double k1 = 0.0, k2 = 0.0, b = B[jj], an = 0.0, cn = 0.0;
-      if (jj >= s) {
-        k1 = A[jj] / B[jj - s];
-        an = -A[jj - s] * k1;
-        b = fma(-C[jj - s], k1, b);
-      }
-      if (jj + s < wl) {
-        k2 = C[jj] / B[jj + s];
-        cn = -C[jj + s] * k2;
-        b = fma(-A[jj + s], k2, b);
-      }
-      P.K1[(long long)l * P.p + j] = k1;
-      P.K2[(long long)l * P.p + j] = k2;
-      An[jj] = an; Bn[jj] = b; Cn[jj] = cn;
-    }
-    __syncthreads();
-    double* t;
-    t = A; A = An; An = t;
-    t = B; B = Bn; Bn = t;
-    t = C; C = Cn; Cn = t;
-  }
-  for (int jj = tid; jj < wl; jj += kThreads) P.binv[j0 + jj] = 1.0 / B[jj];
-  __syncthreads();
-}
-
 __device__ __forceinline__ double edge_w(double xj, double xk, double eps) {
   return 1.0 / (fabs(xj - xk) + eps);
 }
@@ -295,35 +333,55 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   const long long j0 = (long long)b * P.w;
   const long long j1 = j0 + P.w < p ? j0 + P.w : p;
   const int wl = j1 > j0 ? (int)(j1 - j0) : 0;
-  const int nwc = wl >= kThreads ? kWarps : (wl + 31) / 32;          // warps with column data
-  const int nwn = n >= kThreads ? kWarps : (int)((n + 31) / 32);    // warps with row data
-  const int nwg = (G + 31) / 32;
+  const int ncol = wl < kThreads ? wl : kThreads;          // threads holding column data
+  const int nrow = n < kThreads ? (int)n : kThreads;       // threads holding row data
+  const long long wp = P.wpad;
 
-  Acc* us = reinterpret_cast<Acc*>(smraw);
-  Acc* vs = us + P.ldn;
-  Acc* red = vs + P.wpad;
-  double* tv = reinterpret_cast<double*>(red + kThreads * V);
-  double* pw = tv + P.wpad;          // 6 * wpad doubles (PCR)
-  double* rs = pw + 6 * P.wpad;      // kWarps*kNF + kNF doubles
+  // shared memory (solve_smem_bytes)
+  double* usd = reinterpret_cast<double*>(smraw);           // ldn: u staged (double or Acc)
+  double* vsd = usd + P.ldn;                                // wpad: vector slab (double or Acc)
+  double* redd = vsd + wp;                                  // kThreads*V: phase A partials
+  double* tv = redd + (long long)kThreads * V;              // wpad: X^T u per column
+  double* pw = tv + wp;                                     // 6*wpad: PCR work
+  double* cst = pw + 6 * wp;                                // 6*wpad: per-column constants
+  double* rs = cst + 6 * wp;                                // kRF*kThreads + 16
+  unsigned char* nb = reinterpret_cast<unsigned char*>(rs + kRF * kThreads + 16);  // wpad
+  double* s_la = cst;            // lam1 a_j
+  double* s_wl = cst + wp;       // lam2 w(j-1, j) etc.
+  double* s_wr = cst + 2 * wp;
+  double* s_wu = cst + 3 * wp;
+  double* s_wd = cst + 4 * wp;
+  double* s_idg = cst + 5 * wp;  // 1 / diag(Q)
+  double* sc = rs + kRF * kThreads + 8;   // scalar broadcast slots
+  Acc* us = reinterpret_cast<Acc*>(usd);
+  Acc* vs = reinterpret_cast<Acc*>(vsd);
+  Acc* red = reinterpret_cast<Acc*>(redd);
+
   const TX* Xt = reinterpret_cast<const TX*>(P.Xt);
-  Acc* ub[2] = {reinterpret_cast<Acc*>(P.ub0), reinterpret_cast<Acc*>(P.ub1)};
-  double* pbuf[2] = {P.pb0, P.pb1};
   GridBarrier gb{P.bar, P.err, 0u, P.timeout};
   int slot = 0;
+  const long long zchunk = (n + G - 1) / G;
+  const long long zs = (long long)b * zchunk;
+  const long long ze = zs + zchunk < n ? zs + zchunk : n;
 
-  // grid-wide sum of kNF fields (each block contributes v, all blocks get totals)
-  auto grid_sum = [&](double (&v)[kNF]) -> bool {
+  // grid-wide sum of F fields: every block contributes v and receives totals
+  auto grid_sum = [&](auto& v) -> bool {
+    constexpr int F = sizeof(v) / sizeof(double);
     if (tid == 0) {
 #pragma unroll
-      for (int f = 0; f < kNF; ++f) P.part[((long long)slot * kNF + f) * G + b] = v[f];
+      for (int f = 0; f < F; ++f) P.part[((long long)slot * kNF + f) * G + b] = v[f];
     }
     if (!gb.sync()) return false;
 #pragma unroll
-    for (int f = 0; f < kNF; ++f)
+    for (int f = 0; f < F; ++f)
       v[f] = tid < G ? ldcg(&P.part[((long long)slot * kNF + f) * G + tid]) : 0.0;
-    block_sum<kNF>(v, rs, nwg);
+    block_reduce<F>(v, rs, G);
     slot ^= 1;
     return true;
+  };
+  auto zero_u = [&](void* buf) {   // this block's chunk of an n-vector of doubles
+    double* u = reinterpret_cast<double*>(buf);
+    for (long long i = zs + tid; i < ze; i += kThreads) u[i] = 0.0;
   };
 
   // ---- initialisation (Algorithm 1): beta_j = X_j^T y / X_j^T X_j
@@ -333,94 +391,83 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
     if (P.beta_init) v = P.beta_init[j];
     else v = P.d[j] != 0.0 ? P.c[j] / P.d[j] : 0.0;
     P.x[j] = v;
+    unsigned char fl = 0;
+    if (GK == GK_STENCIL) {
+      const long long col = j % q2;
+      if (col != 0) fl |= NB_L;
+      if (col != q2 - 1 && j + 1 < p) fl |= NB_R;
+      if (j >= q2) fl |= NB_U;
+      if (j + q2 < p) fl |= NB_D;
+    }
+    nb[jj] = fl;
   }
   if (P.inject_stall && b == 0) return;   // the others' bounded waits must expire
   if (!gb.sync()) return;
 
-  int cur_u = 0, pcur = 0, mm = 0, cg_total = 0, status = ST_OK;
+  int ucur = 0, pcur = 0, mm = 0, cg_total = 0, status = ST_OK;
   double f = 0.0, f_prev = 0.0, rel = 0.0, relres = 0.0, rss_last = 0.0;
 
   while (true) {
-    // ---------------- reweight (Eq. lin-sys) and S x for the CG start
-    double loc[kNF] = {0.0, 0.0, 0.0, 0.0};   // sum|x_j|, sum_E|x_j - x_k|
+    void* U0 = ucur ? P.ub1 : P.ub0;
+    void* U1 = ucur ? P.ub0 : P.ub1;
+    // ---------------- reweight (Eq. lin-sys), S x, penalties of f
+    double pen[2] = {0.0, 0.0};   // sum|x_j|, sum_E|x_j - x_k|
     for (int jj = tid; jj < wl; jj += kThreads) {
       const long long j = j0 + jj;
       const double xj = ldcg(P.x + j);
       const double aj = 1.0 / (fabs(xj) + P.eps);
-      P.a[j] = aj;
       double deg = 0.0, lap = 0.0;
       if (GK == GK_STENCIL) {
-        const long long col = j % q2;
+        const unsigned char fl = nb[jj];
         double wl_ = 0.0, wr_ = 0.0, wu_ = 0.0, wd_ = 0.0;
-        if (col != 0) {
-          const double xk = ldcg(P.x + j - 1);
-          wl_ = edge_w(xk, xj, P.eps);
-          lap = fma(wl_, xj - xk, lap);
-        }
-        if (col != q2 - 1 && j + 1 < p) {
-          const double xk = ldcg(P.x + j + 1);
-          wr_ = edge_w(xj, xk, P.eps);
-          lap = fma(wr_, xj - xk, lap);
-          loc[1] += fabs(xj - xk);
-        }
-        if (j >= q2) {
-          const double xk = ldcg(P.x + j - q2);
-          wu_ = edge_w(xk, xj, P.eps);
-          lap = fma(wu_, xj - xk, lap);
-        }
-        if (j + q2 < p) {
-          const double xk = ldcg(P.x + j + q2);
-          wd_ = edge_w(xj, xk, P.eps);
-          lap = fma(wd_, xj - xk, lap);
-          loc[1] += fabs(xj - xk);
-        }
-        P.wL[j] = wl_; P.wR[j] = wr_; P.wU[j] = wu_; P.wD[j] = wd_;
+        if (fl & NB_L) { const double xk = ldcg(P.x + j - 1);  wl_ = edge_w(xk, xj, P.eps); lap = fma(wl_, xj - xk, lap); }
+        if (fl & NB_R) { const double xk = ldcg(P.x + j + 1);  wr_ = edge_w(xj, xk, P.eps); lap = fma(wr_, xj - xk, lap); pen[1] += fabs(xj - xk); }
+        if (fl & NB_U) { const double xk = ldcg(P.x + j - q2); wu_ = edge_w(xk, xj, P.eps); lap = fma(wu_, xj - xk, lap); }
+        if (fl & NB_D) { const double xk = ldcg(P.x + j + q2); wd_ = edge_w(xj, xk, P.eps); lap = fma(wd_, xj - xk, lap); pen[1] += fabs(xj - xk); }
         deg = (wl_ + wr_) + (wu_ + wd_);
+        s_wl[jj] = P.lam2 * wl_; s_wr[jj] = P.lam2 * wr_;
+        s_wu[jj] = P.lam2 * wu_; s_wd[jj] = P.lam2 * wd_;
       } else {
         for (long long e = P.rowptr[j]; e < P.rowptr[j + 1]; ++e) {
           const long long k = P.col[e];
           const double xk = ldcg(P.x + k);
           const double we = k > j ? edge_w(xj, xk, P.eps) : edge_w(xk, xj, P.eps);
-          P.wc[e] = we;
+          P.wc[e] = P.lam2 * we;
           deg += we;
           lap = fma(we, xj - xk, lap);
-          if (k > j) loc[1] += fabs(xj - xk);
+          if (k > j) pen[1] += fabs(xj - xk);
         }
       }
-      loc[0] += fabs(xj);
-      const double dq = fma(P.lam2, deg, fma(P.lam1, aj, P.d[j]));
-      P.idg[j] = 1.0 / dq;
-      P.q[j] = fma(P.lam1 * aj, xj, P.lam2 * lap);      // (lam1 A + lam2 B) x
-      vs[jj] = (Acc)xj;
-    }
-    if (P.precond != PC_JACOBI && GK == GK_STENCIL) {
-      __syncthreads();
-      setup_tridiag(P, j0, wl, pw);
+      pen[0] += fabs(xj);
+      const double la = P.lam1 * aj;
+      s_la[jj] = la;
+      const double dq = fma(P.lam2, deg, la + P.d[j]);
+      s_idg[jj] = 1.0 / dq;
+      P.q[j] = fma(la, xj, P.lam2 * lap);      // S x
+      tv[jj] = (P.precond == PC_TRIDIAG) ? dq : dq - P.d[j];   // tridiagonal diagonal
+      vsd[jj] = xj;
     }
     __syncthreads();
-    // ---------------- u0 = X x (for f and for r0)
+    if (P.precond != PC_JACOBI && GK == GK_STENCIL) setup_tridiag(P, j0, wl, tv, s_wl, s_wr, pw);
+    // ---------------- u0 = X x in FP64 (refinement pass)
+    zero_u(U1);
+    phase_a<TX, double>(P, Xt, j0, wl, vsd, redd, reinterpret_cast<double*>(U0));
+    block_reduce<2>(pen, rs, ncol);
+    if (!grid_sum(pen)) return;
+    // ---------------- f(beta(r)) (Eq. obj) and the outer stop test
     {
-      const long long zs = (long long)b * ((n + G - 1) / G);
-      const long long ze = zs + (n + G - 1) / G < n ? zs + (n + G - 1) / G : n;
-      for (long long i = zs + tid; i < ze; i += kThreads) ub[cur_u ^ 1][i] = Acc(0);
-    }
-    phase_a<TX>(P, Xt, j0, wl, vs, red, ub[cur_u]);
-    block_sum<kNF>(loc, rs, nwc);
-    if (!grid_sum(loc)) return;
-    // ---------------- objective f(beta(r)) (Eq. obj) and outer stop
-    {
-      double rv[kNF] = {0.0, 0.0, 0.0, 0.0};
-      const Acc* u = ub[cur_u];
+      double rv[1] = {0.0};
+      const double* u = reinterpret_cast<const double*>(U0);
       for (long long i = tid; i < n; i += kThreads) {
-        const Acc ui = ldcg(u + i);
-        us[i] = ui;
-        const double e = P.y[i] - (double)ui;
+        const double ui = ldcg(u + i);
+        usd[i] = ui;
+        const double e = P.y[i] - ui;
         rv[0] = fma(e, e, rv[0]);
       }
-      for (long long i = n + tid; i < P.ldn; i += kThreads) us[i] = Acc(0);
-      block_sum<kNF>(rv, rs, nwn);
+      for (long long i = n + tid; i < P.ldn; i += kThreads) usd[i] = 0.0;
+      block_reduce<1>(rv, rs, nrow);
       rss_last = rv[0];
-      f = 0.5 * rv[0] + P.lam1 * loc[0] + P.lam2 * loc[1];
+      f = 0.5 * rv[0] + P.lam1 * pen[0] + P.lam2 * pen[1];
     }
     if (!isfinite(f)) { status = ST_NONFINITE; break; }
     if (mm > 0) {
@@ -428,83 +475,93 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       if (rel <= P.tol) break;
     }
     if (mm >= P.max_mm) { status = ST_NOTCONV; break; }
-    // ---------------- r0 = c - Q x0, z0 = M^-1 r0, p1 = z0 (Algorithm 2)
-    phase_c<TX>(P, Xt, j0, wl, us, tv);
+    // ---------------- r0 = c - Q x0 (FP64), z0 = M^-1 r0, p1 = z0 (Algorithm 2)
+    phase_c<TX, double>(P, Xt, j0, wl, usd, tv);
     for (int jj = tid; jj < wl; jj += kThreads) {
       const long long j = j0 + jj;
-      P.r[j] = P.c[j] - tv[jj] - P.q[j];
+      P.r[j] = (P.c[j] - tv[jj]) - P.q[j];
     }
     __syncthreads();
-    apply_precond(P, j0, wl, pw, pw + P.wpad);
-    double rzv[kNF] = {0.0, 0.0, 0.0, 0.0};
-    for (int jj = tid; jj < wl; jj += kThreads) {
-      const long long j = j0 + jj;
-      const double rj = P.r[j], zj = P.z[j];
-      pbuf[pcur][j] = zj;
-      rzv[0] = fma(rj, zj, rzv[0]);
-      rzv[1] = fma(rj, rj, rzv[1]);
+    apply_precond(P, j0, wl, s_idg, pw, pw + wp);
+    double rz2[2] = {0.0, 0.0};
+    {
+      double* pc = pcur ? P.pb1 : P.pb0;
+      for (int jj = tid; jj < wl; jj += kThreads) {
+        const long long j = j0 + jj;
+        const double rj = P.r[j], zj = P.z[j];
+        pc[j] = zj;
+        rz2[0] = fma(rj, zj, rz2[0]);
+        rz2[1] = fma(rj, rj, rz2[1]);
+      }
     }
-    block_sum<kNF>(rzv, rs, nwc);
-    if (!grid_sum(rzv)) return;
-    double rz = rzv[0], rr = rzv[1], gamma = 0.0;
-    cur_u ^= 1;
-    // ---------------- CG iterations
+    block_reduce<2>(rz2, rs, ncol);
+    if (!grid_sum(rz2)) return;
+    double rz = rz2[0], rr = rz2[1], gamma = 0.0;
+    ucur ^= 1;
+    // ---------------- CG iterations (inner products and scalars in FP64)
     int k = 0;
     while (true) {
-      relres = sqrt(rr) / P.cnorm;
-      if (k >= P.max_cg || (k >= P.min_cg && relres <= P.tol_cg)) break;
-      const double* pc = pbuf[pcur];
-      const double* po = pbuf[pcur ^ 1];
-      // S p with halo p recomputed from (z, p_old) for k > 0
-      double sv[kNF] = {0.0, 0.0, 0.0, 0.0};
+      if (tid == 0) {
+        const double rel_r = sqrt(rr) / P.cnorm;
+        sc[0] = rel_r;
+        sc[1] = (k >= P.max_cg || (k >= P.min_cg && rel_r <= P.tol_cg)) ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      relres = sc[0];
+      if (sc[1] != 0.0) break;
+      Acc* Ucur = reinterpret_cast<Acc*>(ucur ? P.ub1 : P.ub0);
+      void* Unext = ucur ? P.ub0 : P.ub1;
+      const double* pc = pcur ? P.pb1 : P.pb0;
+      const double* po = pcur ? P.pb0 : P.pb1;
       auto pval = [&](long long kk) -> double {
         if (kk >= j0 && kk < j1) return pc[kk];
         if (k == 0) return ldcg(pc + kk);
         return fma(gamma, ldcg(po + kk), ldcg(P.z + kk));
       };
+      double sv[1] = {0.0};
       for (int jj = tid; jj < wl; jj += kThreads) {
         const long long j = j0 + jj;
         const double pj = pc[j];
         double lap = 0.0;
         if (GK == GK_STENCIL) {
-          const long long col = j % q2;
-          if (col != 0) lap = fma(P.wL[j], pj - pval(j - 1), lap);
-          if (col != q2 - 1 && j + 1 < p) lap = fma(P.wR[j], pj - pval(j + 1), lap);
-          if (j >= q2) lap = fma(P.wU[j], pj - pval(j - q2), lap);
-          if (j + q2 < p) lap = fma(P.wD[j], pj - pval(j + q2), lap);
+          const unsigned char fl = nb[jj];
+          if (fl & NB_L) lap = fma(s_wl[jj], pj - pval(j - 1), lap);
+          if (fl & NB_R) lap = fma(s_wr[jj], pj - pval(j + 1), lap);
+          if (fl & NB_U) lap = fma(s_wu[jj], pj - pval(j - q2), lap);
+          if (fl & NB_D) lap = fma(s_wd[jj], pj - pval(j + q2), lap);
         } else {
           for (long long e = P.rowptr[j]; e < P.rowptr[j + 1]; ++e)
             lap = fma(P.wc[e], pj - pval(P.col[e]), lap);
         }
-        const double spj = fma(P.lam1 * P.a[j], pj, P.lam2 * lap);
+        const double spj = fma(s_la[jj], pj, lap);
         P.q[j] = spj;
         sv[0] = fma(pj, spj, sv[0]);
         vs[jj] = (Acc)pj;
       }
-      {
-        const long long zs = (long long)b * ((n + G - 1) / G);
-        const long long ze = zs + (n + G - 1) / G < n ? zs + (n + G - 1) / G : n;
-        for (long long i = zs + tid; i < ze; i += kThreads) ub[cur_u ^ 1][i] = Acc(0);
-      }
+      zero_u(Unext);
       __syncthreads();
-      phase_a<TX>(P, Xt, j0, wl, vs, red, ub[cur_u]);
-      block_sum<kNF>(sv, rs, nwc);
+      phase_a<TX, Acc>(P, Xt, j0, wl, vs, red, Ucur);
+      block_reduce<1>(sv, rs, ncol);
       if (!grid_sum(sv)) return;
       // p^T Q p = ||X p||^2 + p^T S p
-      double uu[kNF] = {0.0, 0.0, 0.0, 0.0};
-      {
-        const Acc* u = ub[cur_u];
-        for (long long i = tid; i < n; i += kThreads) {
-          const Acc ui = ldcg(u + i);
-          us[i] = ui;
-          uu[0] = fma((double)ui, (double)ui, uu[0]);
-        }
-        block_sum<kNF>(uu, rs, nwn);
+      double uu[1] = {0.0};
+      for (long long i = tid; i < n; i += kThreads) {
+        const Acc ui = ldcg(Ucur + i);
+        us[i] = ui;
+        uu[0] = fma((double)ui, (double)ui, uu[0]);
       }
-      const double pq = uu[0] + sv[0];
-      if (!(pq > 0.0) || !isfinite(pq)) { status = isfinite(pq) ? ST_BREAKDOWN : ST_NONFINITE; break; }
-      const double nu = rz / pq;
-      phase_c<TX>(P, Xt, j0, wl, us, tv);
+      for (long long i = n + tid; i < P.ldn; i += kThreads) us[i] = Acc(0);
+      block_reduce<1>(uu, rs, nrow);
+      if (tid == 0) {
+        const double pq = uu[0] + sv[0];
+        const bool bad = !(pq > 0.0) || !isfinite(pq);
+        sc[2] = bad ? 0.0 : rz / pq;
+        sc[3] = bad ? (isfinite(pq) ? (double)ST_BREAKDOWN : (double)ST_NONFINITE) : 0.0;
+      }
+      __syncthreads();
+      if (sc[3] != 0.0) { status = (int)sc[3]; break; }
+      const double nu = sc[2];
+      phase_c<TX, Acc>(P, Xt, j0, wl, us, tv);
       for (int jj = tid; jj < wl; jj += kThreads) {
         const long long j = j0 + jj;
         const double pj = pc[j];
@@ -513,27 +570,29 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
         P.r[j] = fma(-nu, qj, P.r[j]);
       }
       __syncthreads();
-      apply_precond(P, j0, wl, pw, pw + P.wpad);
-      double rzn[kNF] = {0.0, 0.0, 0.0, 0.0};
+      apply_precond(P, j0, wl, s_idg, pw, pw + wp);
+      double rzn[2] = {0.0, 0.0};
       for (int jj = tid; jj < wl; jj += kThreads) {
         const long long j = j0 + jj;
         const double rj = P.r[j];
         rzn[0] = fma(rj, P.z[j], rzn[0]);
         rzn[1] = fma(rj, rj, rzn[1]);
       }
-      block_sum<kNF>(rzn, rs, nwc);
+      block_reduce<2>(rzn, rs, ncol);
       if (!grid_sum(rzn)) return;
-      gamma = rzn[0] / rz;
+      if (tid == 0) sc[4] = rzn[0] / rz;
+      __syncthreads();
+      gamma = sc[4];
       rz = rzn[0];
       rr = rzn[1];
       // p_{j+1} = z_j + gamma p_j into the other buffer
-      double* pn = pbuf[pcur ^ 1];
+      double* pn = pcur ? P.pb0 : P.pb1;
       for (int jj = tid; jj < wl; jj += kThreads) {
         const long long j = j0 + jj;
         pn[j] = fma(gamma, pc[j], P.z[j]);
       }
       pcur ^= 1;
-      cur_u ^= 1;
+      ucur ^= 1;
       ++k;
       __syncthreads();
     }
@@ -548,34 +607,34 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
 
   // ---------------- f_eps at the returned iterate (Eq. pert)
   {
-    double loc[kNF] = {0.0, 0.0, 0.0, 0.0};
+    double pe[2] = {0.0, 0.0};
     for (int jj = tid; jj < wl; jj += kThreads) {
       const long long j = j0 + jj;
       const double xj = ldcg(P.x + j);
       const double ax = fabs(xj);
-      loc[0] += ax - P.eps * log1p(ax / P.eps);
+      pe[0] += ax - P.eps * log1p(ax / P.eps);
       if (GK == GK_STENCIL) {
-        const long long col = j % q2;
-        if (col != q2 - 1 && j + 1 < p) {
+        const unsigned char fl = nb[jj];
+        if (fl & NB_R) {
           const double dd = fabs(xj - ldcg(P.x + j + 1));
-          loc[1] += dd - P.eps * log1p(dd / P.eps);
+          pe[1] += dd - P.eps * log1p(dd / P.eps);
         }
-        if (j + q2 < p) {
+        if (fl & NB_D) {
           const double dd = fabs(xj - ldcg(P.x + j + q2));
-          loc[1] += dd - P.eps * log1p(dd / P.eps);
+          pe[1] += dd - P.eps * log1p(dd / P.eps);
         }
       } else {
         for (long long e = P.rowptr[j]; e < P.rowptr[j + 1]; ++e) {
           const long long k = P.col[e];
           if (k > j) {
             const double dd = fabs(xj - ldcg(P.x + k));
-            loc[1] += dd - P.eps * log1p(dd / P.eps);
+            pe[1] += dd - P.eps * log1p(dd / P.eps);
           }
         }
       }
     }
-    block_sum<kNF>(loc, rs, nwc);
-    if (!grid_sum(loc)) return;
+    block_reduce<2>(pe, rs, ncol);
+    if (!grid_sum(pe)) return;
     if (b == 0 && tid == 0) {
       DevStats* S = P.stats;
       S->mm_iters = mm;
@@ -583,7 +642,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       S->status = status;
       S->pad = 0;
       S->f = f;
-      S->f_eps = 0.5 * rss_last + P.lam1 * loc[0] + P.lam2 * loc[1];
+      S->f_eps = 0.5 * rss_last + P.lam1 * pe[0] + P.lam2 * pe[1];
       S->rel_change = rel;
       S->cg_relres = relres;
     }

@@ -248,8 +248,9 @@ def test_host_buffers_match_device(flr):
     ba, sa = a.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-10)
     out = torch.empty(pr.p, dtype=torch.float64).pin_memory()
     bb, sb = b.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-10, out=out)
-    assert sa.f == sb.f
-    assert torch.equal(ba.cpu(), bb)
+    # FP64 atomics across blocks sum in a run-dependent order: equal to rounding
+    assert abs(sa.f - sb.f) <= 1e-12 * abs(sa.f)
+    assert (ba.cpu() - bb).abs().max().item() <= 1e-9 * bb.abs().max().item()
 
 
 def test_repeat_is_deterministic(flr):
@@ -280,8 +281,8 @@ def test_batch_equals_single(flr):
     betas, objs, sts = prob.solve_batch(l1, l2, eps=pr.eps, tol=1e-10)
     for k in range(3):
         b, s = prob.solve(l1[k], l2[k], eps=pr.eps, tol=1e-10)
-        assert objs[k] == s.f
-        assert torch.equal(betas[:, k], b)
+        assert abs(objs[k] - s.f) <= 1e-12 * abs(s.f)
+        assert (betas[:, k] - b).abs().max().item() <= 1e-9 * b.abs().max().item()
 
 
 @pytest.mark.parametrize("bad", ["self_loop", "duplicate", "reversed_duplicate", "out_of_range"])
