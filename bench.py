@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--precond", default="jacobi")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--once", default=None, choices=["config2", "config4"],
+                    help="one solve of a workload (for profiler captures), then exit")
+    ap.add_argument("--max-mm", type=int, default=20000)
+    ap.add_argument("--max-cg", type=int, default=10000)
     return ap.parse_args()
 
 
@@ -196,9 +200,29 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def solve_once(args):
+    """One solve of a workload with capped iterations (the unit a profiler captures)."""
+    import torch
+    import flr_inputs as fi
+    import paper_1306_1970_gb300 as flr
+    flr.load(build_if_missing=True)
+    pr = fi.config(2) if args.once == "config2" else fi.config(4)
+    X = torch.from_numpy(pr.X).cuda()
+    y = torch.from_numpy(pr.y).cuda()
+    prob = flr.Problem(X, y, pr.graph)
+    _, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=args.tol, precond=args.precond,
+                       tol_cg=args.tol_cg, max_mm=args.max_mm, max_cg=args.max_cg)
+    torch.cuda.synchronize()
+    print(json.dumps({"once": args.once, "n": pr.n, "p": pr.p, "mm_iters": st.mm_iters,
+                      "cg_iters": st.cg_iters, "status": st.status, "ms": st.ms, "f": st.f}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.once:
+        solve_once(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank)
         return
