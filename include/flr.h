@@ -44,7 +44,8 @@ typedef enum flr_status {
     FLR_EBREAKDOWN = 5,   /* CG met p^T Q p <= 0 (Q not SPD, e.g. lambda1 = 0 with singular X^T X + lambda2 B) */
     FLR_ENONFINITE = 6,   /* a non-finite value appeared (inputs or arithmetic) */
     FLR_ETIMEOUT = 7,     /* a bounded device-side wait gave up; results are not valid */
-    FLR_ENOTIMPL = 8      /* the requested combination is not implemented */
+    FLR_ENOTIMPL = 8,     /* the requested combination is not implemented */
+    FLR_ESCRATCH = 9      /* flr_solve_noalloc: the problem does not fit its static scratch */
 } flr_status;
 
 /* Storage type of X.  Products with X accumulate in FP32 for F32/BF16/F16
@@ -172,6 +173,46 @@ const char* flr_strerror(int32_t status);
 
 /* Problem sizes of a handle (any out-pointer may be NULL). */
 flr_status flr_get_info(flr_t h, int64_t* n, int64_t* p, int64_t* m, int32_t* dtype);
+
+/* Bytes of the static device scratch array used by flr_solve_noalloc. */
+#define FLR_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* The same MM solve as flr_solve, for callers that cannot allocate device
+ * memory: it calls no cudaMalloc/cudaFree and no allocating library routine.
+ * (The paper has no counterpart; this is a deployment entry point.)  Typical
+ * such callers run inside a framework whose caching allocator has already
+ * reserved the GPU's memory, so a new cudaMalloc would fail or fragment that
+ * pool, or in a serving loop that must not take the driver's allocation
+ * path, which can synchronize the device.
+ *
+ * All working memory comes from one static device array of
+ * FLR_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (with that device current) and caches it; make that first call
+ * before any stream capture.  Every call shares the array and it keeps the
+ * previous call's contents (what must start at zero is cleared on each
+ * call); calls whose GPU work overlaps -- on other streams or from other
+ * threads -- race on it and must be serialised by the caller.
+ *
+ *   Xt        X stored column-major, device memory: column j (n values) starts
+ *             at element j*ldn.  ldn >= n, ldn * element size a multiple of 16
+ *             bytes, Xt 16-byte aligned; elements in rows n..ldn-1 must be
+ *             finite (zero is typical).  dtype as in flr_create.
+ *   y         n doubles, device memory.
+ *   E         FLR_E_CHAIN or FLR_E_LATTICE (FLR_E_EDGES: FLR_ENOTIMPL).
+ *   lambda1, lambda2, eps, tol, opts: as in flr_solve (beta starts at
+ *             X_j^T y / X_j^T X_j).
+ *   beta_out  p doubles, device memory.
+ *   stream    cudaStream_t all work is issued on; the call returns when done.
+ *   stats     optional, host memory (ms is host wall time).
+ * Scratch needed (bytes, each part rounded up to 256): 256 + 32768 + 256
+ * + 9*8*p + 2*8*ldn, plus 2*8*p*ceil(log2(ceil(p/grid))) for the tridiagonal
+ * preconditioners.  A problem that needs more than FLR_NOALLOC_SCRATCH_BYTES
+ * returns FLR_ESCRATCH before any GPU work.  Other errors as flr_solve. */
+flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n, int64_t p, int64_t ldn,
+                             const double* y, const flr_graph* E, double lambda1, double lambda2,
+                             double eps, double tol, const flr_opts* opts, double* beta_out,
+                             void* stream, flr_stats* stats);
 
 #ifdef __cplusplus
 }

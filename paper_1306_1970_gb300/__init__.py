@@ -19,7 +19,7 @@ from typing import Optional
 from . import _build
 
 FLR_OK, FLR_EINVAL, FLR_ENOMEM, FLR_ECUDA, FLR_ENOTCONV = 0, 1, 2, 3, 4
-FLR_EBREAKDOWN, FLR_ENONFINITE, FLR_ETIMEOUT, FLR_ENOTIMPL = 5, 6, 7, 8
+FLR_EBREAKDOWN, FLR_ENONFINITE, FLR_ETIMEOUT, FLR_ENOTIMPL, FLR_ESCRATCH = 5, 6, 7, 8, 9
 FLR_F64, FLR_F32, FLR_BF16, FLR_F16 = 0, 1, 2, 3
 FLR_MEM_DEVICE, FLR_MEM_HOST = 0, 1
 FLR_E_CHAIN, FLR_E_LATTICE, FLR_E_EDGES = 0, 1, 2
@@ -28,7 +28,7 @@ DTYPE_CODES = {"f64": FLR_F64, "f32": FLR_F32, "bf16": FLR_BF16, "f16": FLR_F16}
 
 # every symbol declared in include/flr.h
 EXPORTS = ("flr_default_opts", "flr_strerror", "flr_create", "flr_solve", "flr_solve_batch",
-           "flr_destroy", "flr_get_info")
+           "flr_destroy", "flr_get_info", "flr_solve_noalloc")
 
 
 class FlrGraph(ctypes.Structure):
@@ -94,6 +94,11 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.flr_destroy.restype = None
     lib.flr_get_info.argtypes = [c.c_void_p] + [c.c_void_p] * 4
     lib.flr_get_info.restype = c.c_int32
+    lib.flr_solve_noalloc.argtypes = [c.c_void_p, c.c_int32, c.c_int64, c.c_int64, c.c_int64,
+                                      c.c_void_p, c.POINTER(FlrGraph), c.c_double, c.c_double,
+                                      c.c_double, c.c_double, c.POINTER(FlrOpts), c.c_void_p,
+                                      c.c_void_p, c.POINTER(FlrStats)]
+    lib.flr_solve_noalloc.restype = c.c_int32
     _LIB = lib
     return lib
 

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libflr.so")
-SOURCES = ["flr_api.cu"]
+SOURCES = ["flr_api.cu", "flr_noalloc.cu"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC", "-shared"]
 
@@ -41,14 +41,32 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=HERE)
     os.close(fd)
-    cmd = [nvcc()] + NVCC_FLAGS + ["-I", INCLUDE] + [os.path.join(CSRC, s) for s in SOURCES] + ["-o", tmp]
-    if verbose:
-        print(" ".join(cmd), flush=True)
+    objdir = tempfile.mkdtemp(prefix="flr_build_")
+    objs = [os.path.join(objdir, s + ".o") for s in SOURCES]
+    # translation units compile in parallel, then one link step
+    procs = []
+    for s, o in zip(SOURCES, objs):
+        cmd = [nvcc()] + NVCC_FLAGS[:-1] + ["-c", "-I", INCLUDE, os.path.join(CSRC, s), "-o", o]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        procs.append(subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE))
+    errs = []
+    for pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            errs.append(err.decode(errors="replace"))
     try:
-        subprocess.run(cmd, check=True, capture_output=not verbose)
-    except subprocess.CalledProcessError as e:
-        os.unlink(tmp)
-        msg = (e.stderr or b"").decode(errors="replace")
-        raise RuntimeError(f"nvcc failed building libflr.so:\n{msg}") from None
+        if errs:
+            raise RuntimeError("nvcc failed building libflr.so:\n" + "\n".join(errs))
+        link = [nvcc(), "-shared", "-gencode", "arch=compute_103a,code=sm_103a"] + objs + ["-o", tmp]
+        r = subprocess.run(link, capture_output=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc link failed:\n" + r.stderr.decode(errors="replace"))
+    except Exception:
+        if os.path.exists(tmp):
+            os.unlink(tmp)
+        raise
+    finally:
+        shutil.rmtree(objdir, ignore_errors=True)
     os.replace(tmp, LIB)
     return LIB

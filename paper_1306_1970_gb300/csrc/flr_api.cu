@@ -251,6 +251,7 @@ const char* flr_strerror(int32_t s) {
     case FLR_ENONFINITE: return "FLR_ENONFINITE: non-finite value";
     case FLR_ETIMEOUT: return "FLR_ETIMEOUT: a bounded device-side wait gave up";
     case FLR_ENOTIMPL: return "FLR_ENOTIMPL: combination not implemented";
+    case FLR_ESCRATCH: return "FLR_ESCRATCH: problem too large for the static scratch of flr_solve_noalloc";
     default: return "unknown flr_status";
   }
 }
