@@ -84,8 +84,8 @@ struct SolveParams {
 // shared-memory bytes of mm_solve_kernel (the host uses the same formula)
 __host__ __device__ inline size_t solve_smem_bytes(long long ldn, long long wpad, int V) {
   return (size_t)ldn * 8 + (size_t)wpad * 8 + (size_t)kThreads * V * 8 + (size_t)wpad * 8 +
-         6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 + ((size_t)kRF * kThreads + 16) * 8 +
-         (size_t)wpad;
+         6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 + 5 * (size_t)wpad * 8 +
+         ((size_t)kRF * kThreads + 16) * 8 + (size_t)wpad;
 }
 
 template <typename TX, typename A>
@@ -136,12 +136,12 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
       for (int e = 0; e < V; ++e) acc[e] = A(0);
       const TX* base = Xt + j0 * P.ldn + (long long)rv * V;
       int j = 0;
-      for (; j + 4 <= wl; j += 4) {
-        uint4 raw[4];
+      for (; j + 8 <= wl; j += 8) {
+        uint4 raw[8];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) raw[k] = ld_stream16(base + (long long)(j + k) * P.ldn);
+        for (int k = 0; k < 8; ++k) raw[k] = ld_stream16(base + (long long)(j + k) * P.ldn);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 8; ++k) {
           A xv[V];
           cvt_to<TX, A>(raw[k], xv);
           const A s = vs[j + k];
@@ -171,12 +171,12 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
     if (cg < ncg) {
       const TX* base = Xt + j0 * P.ldn + (long long)rv * V;
       int j = cg;
-      for (; j + 3 * ncg < wl; j += 4 * ncg) {
-        uint4 raw[4];
+      for (; j + 7 * ncg < wl; j += 8 * ncg) {
+        uint4 raw[8];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) raw[k] = ld_stream16(base + (long long)(j + k * ncg) * P.ldn);
+        for (int k = 0; k < 8; ++k) raw[k] = ld_stream16(base + (long long)(j + k * ncg) * P.ldn);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 8; ++k) {
           A xv[V];
           cvt_to<TX, A>(raw[k], xv);
           const A s = vs[j + k * ncg];
@@ -205,40 +205,53 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
   }
 }
 
-// tv[jj] = X[:, j0+jj]^T u  for jj in [0, wl)   (u staged in shared memory)
+// tv[jj] = X[:, j0+jj]^T u  for jj in [0, wl)   (u staged in shared memory).
+// One warp per pair of columns; each lane keeps CPW x UR 16-byte loads in flight.
 template <typename TX, typename A>
 __device__ __forceinline__ void phase_c(const SolveParams& P, const TX* __restrict__ Xt,
                                         long long j0, int wl, const A* us, double* tv) {
   constexpr int V = XT<TX>::V;
-  constexpr int CPW = 4;  // columns per warp in flight
+  constexpr int CPW = 2;  // columns per warp
+  constexpr int UR = 4;   // row vectors per lane per round
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nv = (int)(P.ldn / V);
   for (int base = warp * CPW; base < wl; base += kWarps * CPW) {
     A acc[CPW];
 #pragma unroll
     for (int c = 0; c < CPW; ++c) acc[c] = A(0);
-    for (int rv = lane; rv < nv; rv += 32) {
-      A uu[V];
-#pragma unroll
-      for (int e = 0; e < V; ++e) uu[e] = us[rv * V + e];
-      uint4 raw[CPW];
+    for (int rv0 = lane; rv0 < nv; rv0 += 32 * UR) {
+      uint4 raw[CPW][UR];
 #pragma unroll
       for (int c = 0; c < CPW; ++c)
-        if (base + c < wl) raw[c] = ld_stream16(Xt + (j0 + base + c) * P.ldn + (long long)rv * V);
 #pragma unroll
-      for (int c = 0; c < CPW; ++c) {
-        if (base + c < wl) {
-          A xv[V];
-          cvt_to<TX, A>(raw[c], xv);
+        for (int u = 0; u < UR; ++u) {
+          const int rv = rv0 + 32 * u;
+          if (base + c < wl && rv < nv)
+            raw[c][u] = ld_stream16(Xt + (j0 + base + c) * P.ldn + (long long)rv * V);
+        }
 #pragma unroll
-          for (int e = 0; e < V; ++e) acc[c] = fma(xv[e], uu[e], acc[c]);
+      for (int u = 0; u < UR; ++u) {
+        const int rv = rv0 + 32 * u;
+        if (rv < nv) {
+          A uu[V];
+#pragma unroll
+          for (int e = 0; e < V; ++e) uu[e] = us[rv * V + e];
+#pragma unroll
+          for (int c = 0; c < CPW; ++c) {
+            if (base + c < wl) {
+              A xv[V];
+              cvt_to<TX, A>(raw[c][u], xv);
+#pragma unroll
+              for (int e = 0; e < V; ++e) acc[c] = fma(xv[e], uu[e], acc[c]);
+            }
+          }
         }
       }
     }
 #pragma unroll
     for (int c = 0; c < CPW; ++c) {
-      const A s = warp_sum(acc[c]);
-      if (lane == 0 && base + c < wl) tv[base + c] = (double)s;
+      const A sum = warp_sum(acc[c]);
+      if (lane == 0 && base + c < wl) tv[base + c] = (double)sum;
     }
   }
   __syncthreads();
@@ -289,16 +302,24 @@ __device__ __forceinline__ void setup_tridiag(const SolveParams& P, long long j0
   __syncthreads();
 }
 
-// z[own] = M^-1 r[own] (Jacobi, or PCR with the precomputed multipliers)
+// z = M^-1 r for the block's own coefficients: r from shared memory, z to
+// shared memory and to global memory (neighbouring blocks read it as halo).
+// Jacobi: r / diag(Q).  Tridiagonal: parallel cyclic reduction with the
+// multipliers precomputed once per MM iteration (K1, K2, binv).
 __device__ __forceinline__ void apply_precond(const SolveParams& P, long long j0, int wl,
-                                              const double* sidg, double* w0, double* w1) {
+                                              const double* sidg, const double* rsm,
+                                              double* zsm, double* w0, double* w1) {
   const int tid = threadIdx.x;
   if (P.precond == PC_JACOBI) {
-    for (int jj = tid; jj < wl; jj += kThreads) P.z[j0 + jj] = P.r[j0 + jj] * sidg[jj];
+    for (int jj = tid; jj < wl; jj += kThreads) {
+      const double z = rsm[jj] * sidg[jj];
+      zsm[jj] = z;
+      P.z[j0 + jj] = z;
+    }
     __syncthreads();
     return;
   }
-  for (int jj = tid; jj < wl; jj += kThreads) w0[jj] = P.r[j0 + jj];
+  for (int jj = tid; jj < wl; jj += kThreads) w0[jj] = rsm[jj];
   __syncthreads();
   double* cur = w0;
   double* nxt = w1;
@@ -314,8 +335,49 @@ __device__ __forceinline__ void apply_precond(const SolveParams& P, long long j0
     __syncthreads();
     double* t = cur; cur = nxt; nxt = t;
   }
-  for (int jj = tid; jj < wl; jj += kThreads) P.z[j0 + jj] = cur[jj] * P.binv[j0 + jj];
+  for (int jj = tid; jj < wl; jj += kThreads) {
+    const double z = cur[jj] * P.binv[j0 + jj];
+    zsm[jj] = z;
+    P.z[j0 + jj] = z;
+  }
   __syncthreads();
+}
+
+// Copy an n-vector (ldn entries, padding zero) from global to shared memory with
+// 16-byte coherent loads; returns this thread's partial sum of squares of the
+// first n entries (FP64), and optionally of (y - u)^2.
+template <typename A>
+__device__ __forceinline__ double stage_u(const A* __restrict__ u, A* us, long long n, long long ldn,
+                                          const double* y, bool resid) {
+  constexpr int VA = 16 / sizeof(A);
+  const int nvec = (int)(ldn / VA);
+  double acc = 0.0;
+  for (int v = threadIdx.x; v < nvec; v += kThreads) {
+    A t[VA];
+    if constexpr (VA == 4) {
+      const float4 q = __ldcg(reinterpret_cast<const float4*>(u) + v);
+      const float tt[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int e = 0; e < VA; ++e) t[e] = (A)tt[e % 4];
+    } else {
+      const double2 q = __ldcg(reinterpret_cast<const double2*>(u) + v);
+      const double tt[2] = {q.x, q.y};
+#pragma unroll
+      for (int e = 0; e < VA; ++e) t[e] = (A)tt[e % 2];
+    }
+#pragma unroll
+    for (int e = 0; e < VA; ++e) {
+      const long long i = (long long)v * VA + e;
+      if (i < n) {
+        us[i] = t[e];
+        const double d = resid ? y[i] - (double)t[e] : (double)t[e];
+        acc = fma(d, d, acc);
+      } else {
+        us[i] = A(0);
+      }
+    }
+  }
+  return acc;
 }
 
 __device__ __forceinline__ double edge_w(double xj, double xk, double eps) {
@@ -334,7 +396,6 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   const long long j1 = j0 + P.w < p ? j0 + P.w : p;
   const int wl = j1 > j0 ? (int)(j1 - j0) : 0;
   const int ncol = wl < kThreads ? wl : kThreads;          // threads holding column data
-  const int nrow = n < kThreads ? (int)n : kThreads;       // threads holding row data
   const long long wp = P.wpad;
 
   // shared memory (solve_smem_bytes)
@@ -344,7 +405,8 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   double* tv = redd + (long long)kThreads * V;              // wpad: X^T u per column
   double* pw = tv + wp;                                     // 6*wpad: PCR work
   double* cst = pw + 6 * wp;                                // 6*wpad: per-column constants
-  double* rs = cst + 6 * wp;                                // kRF*kThreads + 16
+  double* own = cst + 6 * wp;                               // 5*wpad: own CG vectors
+  double* rs = own + 5 * wp;                                // kRF*kThreads + 16
   unsigned char* nb = reinterpret_cast<unsigned char*>(rs + kRF * kThreads + 16);  // wpad
   double* s_la = cst;            // lam1 a_j
   double* s_wl = cst + wp;       // lam2 w(j-1, j) etc.
@@ -352,6 +414,11 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   double* s_wu = cst + 3 * wp;
   double* s_wd = cst + 4 * wp;
   double* s_idg = cst + 5 * wp;  // 1 / diag(Q)
+  double* xs = own;              // x (also written to global for the halo of the reweight)
+  double* rsm = own + wp;        // r
+  double* zs = own + 2 * wp;     // z (also global: halo of p)
+  double* ps = own + 3 * wp;     // p (also global, double-buffered)
+  double* qs = own + 4 * wp;     // S p  (S x at the CG start)
   double* sc = rs + kRF * kThreads + 8;   // scalar broadcast slots
   Acc* us = reinterpret_cast<Acc*>(usd);
   Acc* vs = reinterpret_cast<Acc*>(vsd);
@@ -361,8 +428,8 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   GridBarrier gb{P.bar, P.err, 0u, P.timeout};
   int slot = 0;
   const long long zchunk = (n + G - 1) / G;
-  const long long zs = (long long)b * zchunk;
-  const long long ze = zs + zchunk < n ? zs + zchunk : n;
+  const long long zs0 = (long long)b * zchunk;
+  const long long ze0 = zs0 + zchunk < n ? zs0 + zchunk : n;
 
   // grid-wide sum of F fields: every block contributes v and receives totals
   auto grid_sum = [&](auto& v) -> bool {
@@ -381,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   };
   auto zero_u = [&](void* buf) {   // this block's chunk of an n-vector of doubles
     double* u = reinterpret_cast<double*>(buf);
-    for (long long i = zs + tid; i < ze; i += kThreads) u[i] = 0.0;
+    for (long long i = zs0 + tid; i < ze0; i += kThreads) u[i] = 0.0;
   };
 
   // ---- initialisation (Algorithm 1): beta_j = X_j^T y / X_j^T X_j
@@ -420,10 +487,14 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       if (GK == GK_STENCIL) {
         const unsigned char fl = nb[jj];
         double wl_ = 0.0, wr_ = 0.0, wu_ = 0.0, wd_ = 0.0;
-        if (fl & NB_L) { const double xk = ldcg(P.x + j - 1);  wl_ = edge_w(xk, xj, P.eps); lap = fma(wl_, xj - xk, lap); }
-        if (fl & NB_R) { const double xk = ldcg(P.x + j + 1);  wr_ = edge_w(xj, xk, P.eps); lap = fma(wr_, xj - xk, lap); pen[1] += fabs(xj - xk); }
-        if (fl & NB_U) { const double xk = ldcg(P.x + j - q2); wu_ = edge_w(xk, xj, P.eps); lap = fma(wu_, xj - xk, lap); }
-        if (fl & NB_D) { const double xk = ldcg(P.x + j + q2); wd_ = edge_w(xj, xk, P.eps); lap = fma(wd_, xj - xk, lap); pen[1] += fabs(xj - xk); }
+        const double xl = (fl & NB_L) ? ldcg(P.x + j - 1) : 0.0;
+        const double xr = (fl & NB_R) ? ldcg(P.x + j + 1) : 0.0;
+        const double xu = (fl & NB_U) ? ldcg(P.x + j - q2) : 0.0;
+        const double xd = (fl & NB_D) ? ldcg(P.x + j + q2) : 0.0;
+        if (fl & NB_L) { wl_ = edge_w(xl, xj, P.eps); lap = fma(wl_, xj - xl, lap); }
+        if (fl & NB_R) { wr_ = edge_w(xj, xr, P.eps); lap = fma(wr_, xj - xr, lap); pen[1] += fabs(xj - xr); }
+        if (fl & NB_U) { wu_ = edge_w(xu, xj, P.eps); lap = fma(wu_, xj - xu, lap); }
+        if (fl & NB_D) { wd_ = edge_w(xj, xd, P.eps); lap = fma(wd_, xj - xd, lap); pen[1] += fabs(xj - xd); }
         deg = (wl_ + wr_) + (wu_ + wd_);
         s_wl[jj] = P.lam2 * wl_; s_wr[jj] = P.lam2 * wr_;
         s_wu[jj] = P.lam2 * wu_; s_wd[jj] = P.lam2 * wd_;
@@ -443,9 +514,10 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       s_la[jj] = la;
       const double dq = fma(P.lam2, deg, la + P.d[j]);
       s_idg[jj] = 1.0 / dq;
-      P.q[j] = fma(la, xj, P.lam2 * lap);      // S x
+      qs[jj] = fma(la, xj, P.lam2 * lap);      // S x
       tv[jj] = (P.precond == PC_TRIDIAG) ? dq : dq - P.d[j];   // tridiagonal diagonal
       vsd[jj] = xj;
+      xs[jj] = xj;
     }
     __syncthreads();
     if (P.precond != PC_JACOBI && GK == GK_STENCIL) setup_tridiag(P, j0, wl, tv, s_wl, s_wr, pw);
@@ -456,16 +528,8 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
     if (!grid_sum(pen)) return;
     // ---------------- f(beta(r)) (Eq. obj) and the outer stop test
     {
-      double rv[1] = {0.0};
-      const double* u = reinterpret_cast<const double*>(U0);
-      for (long long i = tid; i < n; i += kThreads) {
-        const double ui = ldcg(u + i);
-        usd[i] = ui;
-        const double e = P.y[i] - ui;
-        rv[0] = fma(e, e, rv[0]);
-      }
-      for (long long i = n + tid; i < P.ldn; i += kThreads) usd[i] = 0.0;
-      block_reduce<1>(rv, rs, nrow);
+      double rv[1] = {stage_u<double>(reinterpret_cast<const double*>(U0), usd, n, P.ldn, P.y, true)};
+      block_reduce<1>(rv, rs, kThreads);
       rss_last = rv[0];
       f = 0.5 * rv[0] + P.lam1 * pen[0] + P.lam2 * pen[1];
     }
@@ -477,19 +541,16 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
     if (mm >= P.max_mm) { status = ST_NOTCONV; break; }
     // ---------------- r0 = c - Q x0 (FP64), z0 = M^-1 r0, p1 = z0 (Algorithm 2)
     phase_c<TX, double>(P, Xt, j0, wl, usd, tv);
-    for (int jj = tid; jj < wl; jj += kThreads) {
-      const long long j = j0 + jj;
-      P.r[j] = (P.c[j] - tv[jj]) - P.q[j];
-    }
+    for (int jj = tid; jj < wl; jj += kThreads) rsm[jj] = (P.c[j0 + jj] - tv[jj]) - qs[jj];
     __syncthreads();
-    apply_precond(P, j0, wl, s_idg, pw, pw + wp);
+    apply_precond(P, j0, wl, s_idg, rsm, zs, pw, pw + wp);
     double rz2[2] = {0.0, 0.0};
     {
-      double* pc = pcur ? P.pb1 : P.pb0;
+      double* pg = pcur ? P.pb1 : P.pb0;
       for (int jj = tid; jj < wl; jj += kThreads) {
-        const long long j = j0 + jj;
-        const double rj = P.r[j], zj = P.z[j];
-        pc[j] = zj;
+        const double rj = rsm[jj], zj = zs[jj];
+        ps[jj] = zj;
+        pg[j0 + jj] = zj;
         rz2[0] = fma(rj, zj, rz2[0]);
         rz2[1] = fma(rj, rj, rz2[1]);
       }
@@ -513,28 +574,34 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       void* Unext = ucur ? P.ub0 : P.ub1;
       const double* pc = pcur ? P.pb1 : P.pb0;
       const double* po = pcur ? P.pb0 : P.pb1;
+      // p at a neighbour: own values from shared memory; another block's value is
+      // z + gamma p_old (bit-identical to its owner's update), or p itself at k = 0
       auto pval = [&](long long kk) -> double {
-        if (kk >= j0 && kk < j1) return pc[kk];
+        if (kk >= j0 && kk < j1) return ps[kk - j0];
         if (k == 0) return ldcg(pc + kk);
         return fma(gamma, ldcg(po + kk), ldcg(P.z + kk));
       };
       double sv[1] = {0.0};
       for (int jj = tid; jj < wl; jj += kThreads) {
         const long long j = j0 + jj;
-        const double pj = pc[j];
+        const double pj = ps[jj];
         double lap = 0.0;
         if (GK == GK_STENCIL) {
           const unsigned char fl = nb[jj];
-          if (fl & NB_L) lap = fma(s_wl[jj], pj - pval(j - 1), lap);
-          if (fl & NB_R) lap = fma(s_wr[jj], pj - pval(j + 1), lap);
-          if (fl & NB_U) lap = fma(s_wu[jj], pj - pval(j - q2), lap);
-          if (fl & NB_D) lap = fma(s_wd[jj], pj - pval(j + q2), lap);
+          const double pl = (fl & NB_L) ? pval(j - 1) : pj;
+          const double pr = (fl & NB_R) ? pval(j + 1) : pj;
+          const double pu = (fl & NB_U) ? pval(j - q2) : pj;
+          const double pd = (fl & NB_D) ? pval(j + q2) : pj;
+          lap = fma(s_wl[jj], pj - pl, lap);
+          lap = fma(s_wr[jj], pj - pr, lap);
+          lap = fma(s_wu[jj], pj - pu, lap);
+          lap = fma(s_wd[jj], pj - pd, lap);
         } else {
           for (long long e = P.rowptr[j]; e < P.rowptr[j + 1]; ++e)
             lap = fma(P.wc[e], pj - pval(P.col[e]), lap);
         }
         const double spj = fma(s_la[jj], pj, lap);
-        P.q[j] = spj;
+        qs[jj] = spj;
         sv[0] = fma(pj, spj, sv[0]);
         vs[jj] = (Acc)pj;
       }
@@ -544,14 +611,8 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       block_reduce<1>(sv, rs, ncol);
       if (!grid_sum(sv)) return;
       // p^T Q p = ||X p||^2 + p^T S p
-      double uu[1] = {0.0};
-      for (long long i = tid; i < n; i += kThreads) {
-        const Acc ui = ldcg(Ucur + i);
-        us[i] = ui;
-        uu[0] = fma((double)ui, (double)ui, uu[0]);
-      }
-      for (long long i = n + tid; i < P.ldn; i += kThreads) us[i] = Acc(0);
-      block_reduce<1>(uu, rs, nrow);
+      double uu[1] = {stage_u<Acc>(Ucur, us, n, P.ldn, P.y, false)};
+      block_reduce<1>(uu, rs, kThreads);
       if (tid == 0) {
         const double pq = uu[0] + sv[0];
         const bool bad = !(pq > 0.0) || !isfinite(pq);
@@ -563,19 +624,17 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       const double nu = sc[2];
       phase_c<TX, Acc>(P, Xt, j0, wl, us, tv);
       for (int jj = tid; jj < wl; jj += kThreads) {
-        const long long j = j0 + jj;
-        const double pj = pc[j];
-        const double qj = tv[jj] + P.q[j];
-        P.x[j] = fma(nu, pj, P.x[j]);
-        P.r[j] = fma(-nu, qj, P.r[j]);
+        const double xn = fma(nu, ps[jj], xs[jj]);
+        xs[jj] = xn;
+        P.x[j0 + jj] = xn;
+        rsm[jj] = fma(-nu, tv[jj] + qs[jj], rsm[jj]);
       }
       __syncthreads();
-      apply_precond(P, j0, wl, s_idg, pw, pw + wp);
+      apply_precond(P, j0, wl, s_idg, rsm, zs, pw, pw + wp);
       double rzn[2] = {0.0, 0.0};
       for (int jj = tid; jj < wl; jj += kThreads) {
-        const long long j = j0 + jj;
-        const double rj = P.r[j];
-        rzn[0] = fma(rj, P.z[j], rzn[0]);
+        const double rj = rsm[jj];
+        rzn[0] = fma(rj, zs[jj], rzn[0]);
         rzn[1] = fma(rj, rj, rzn[1]);
       }
       block_reduce<2>(rzn, rs, ncol);
@@ -585,11 +644,12 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       gamma = sc[4];
       rz = rzn[0];
       rr = rzn[1];
-      // p_{j+1} = z_j + gamma p_j into the other buffer
+      // p_{j+1} = z_j + gamma p_j (shared copy and the other global buffer)
       double* pn = pcur ? P.pb0 : P.pb1;
       for (int jj = tid; jj < wl; jj += kThreads) {
-        const long long j = j0 + jj;
-        pn[j] = fma(gamma, pc[j], P.z[j]);
+        const double v = fma(gamma, ps[jj], zs[jj]);
+        ps[jj] = v;
+        pn[j0 + jj] = v;
       }
       pcur ^= 1;
       ucur ^= 1;
