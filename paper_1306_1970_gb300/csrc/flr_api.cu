@@ -11,6 +11,7 @@
 
 #include "../../include/flr.h"
 #include "flr_solve.cuh"
+#include "flr_batch.cuh"
 
 using namespace flr;
 
@@ -102,6 +103,18 @@ struct flr_handle {
   unsigned char* hctl = nullptr;    // pinned copy of ctl
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<void*> allocs;
+  // batched tensor-core path (allocated on first use)
+  bool batch_ready = false;
+  long long ldp = 0;
+  int bS = 1;
+  long long bkchunk = 0;
+  __nv_bfloat16* Xr = nullptr;
+  double* bvec[13] = {nullptr};
+  __nv_bfloat16 *Ps = nullptr, *Us = nullptr;
+  float* Upart = nullptr;
+  double *U0part = nullptr, *U0 = nullptr, *bred = nullptr, *blam = nullptr;
+  unsigned char* bctl = nullptr;
+  BatchStats* bstats = nullptr;
 };
 
 namespace {
@@ -220,6 +233,139 @@ flr_status launch_solve(flr_handle* h, SolveParams& P, int G, size_t smem) {
                             : launch_solve_t<__half, GK_STENCIL>(h, P, G, smem);
   }
   return FLR_EINVAL;
+}
+
+
+flr_status batch_prepare(flr_handle* h) {
+  if (h->batch_ready) return FLR_OK;
+  flr_status s;
+  const long long n = h->n, p = h->p;
+  h->ldp = (p + 7) / 8 * 8;
+  const long long mtiles = (n + kTM - 1) / kTM;
+  int S = (int)std::max<long long>(1, (long long)h->sm_count / mtiles);
+  long long kchunk = (h->ldp + S - 1) / S;
+  kchunk = (kchunk + 63) / 64 * 64;
+  S = (int)((h->ldp + kchunk - 1) / kchunk);
+  h->bS = S;
+  h->bkchunk = kchunk;
+  if ((s = dalloc(h, &h->Xr, (size_t)(n * h->ldp))) != FLR_OK) return s;
+  for (int i = 0; i < 13; ++i)
+    if ((s = dalloc(h, &h->bvec[i], (size_t)kNRMax * p)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->Ps, (size_t)kSlices * kNRMax * h->ldp)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->Us, (size_t)kSlices * kNRMax * h->ldn)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->Upart, (size_t)S * kNRMax * n)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->U0part, (size_t)S * kNRMax * n)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->U0, (size_t)kNRMax * n)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->bred, (size_t)kRedSlots * 4 * kNRMax)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->blam, (size_t)2 * kNRMax)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->bctl, 256)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->bstats, (size_t)kNRMax)) != FLR_OK) return s;
+  // row-major copy of X (the A operand of X P) from the column-major copy
+  FLR_TRY(cudaMemsetAsync(h->Xr, 0, sizeof(__nv_bfloat16) * n * h->ldp, h->stream));
+  FLR_TRY(cudaMemsetAsync(h->Ps, 0, sizeof(__nv_bfloat16) * kSlices * kNRMax * h->ldp, h->stream));
+  FLR_TRY(cudaMemsetAsync(h->Us, 0, sizeof(__nv_bfloat16) * kSlices * kNRMax * h->ldn, h->stream));
+  dim3 tb(32, 8);
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((p + 31) / 32));
+  transpose_kernel<unsigned short><<<grid, tb, 0, h->stream>>>(
+      static_cast<const unsigned short*>(h->Xt), p, n, h->ldn,
+      reinterpret_cast<unsigned short*>(h->Xr), h->ldp);
+  FLR_TRY(cudaGetLastError());
+  h->batch_ready = true;
+  return FLR_OK;
+}
+
+// Solve K <= 64 problems in one launch of mm_batch_kernel.
+flr_status batch_group(flr_handle* h, int K, const double* l1, const double* l2, double eps,
+                       double tol, const flr_opts& o, double* betas, int io_mem,
+                       double* objectives, flr_stats* stats) {
+  flr_status s = batch_prepare(h);
+  if (s != FLR_OK) return s;
+  const int NR = K <= 32 ? 32 : 64;
+  const long long n = h->n, p = h->p;
+  std::vector<double> lam((size_t)2 * kNRMax, 0.0);
+  for (int k = 0; k < K; ++k) { lam[k] = l1[k]; lam[kNRMax + k] = l2[k]; }
+  FLR_TRY(cudaMemcpyAsync(h->blam, lam.data(), sizeof(double) * 2 * kNRMax, cudaMemcpyHostToDevice,
+                          h->stream));
+  FLR_TRY(cudaMemsetAsync(h->bred, 0, sizeof(double) * kRedSlots * 4 * kNRMax, h->stream));
+  FLR_TRY(cudaMemsetAsync(h->bctl, 0, 256, h->stream));
+  FLR_TRY(cudaMemsetAsync(h->bstats, 0xff, sizeof(BatchStats) * kNRMax, h->stream));
+  BatchParams P{};
+  P.Xr = h->Xr; P.Xt = static_cast<const __nv_bfloat16*>(h->Xt);
+  P.n = n; P.p = p; P.ldp = h->ldp; P.ldn = h->ldn;
+  P.q2 = h->gkind == FLR_E_LATTICE ? h->q2 : p;
+  P.K = K; P.NR = NR;
+  P.y = h->y; P.c = h->c; P.d = h->d; P.cnorm = h->cnorm > 0 ? h->cnorm : 1.0;
+  P.lam1 = h->blam; P.lam2 = h->blam + kNRMax;
+  P.eps = eps; P.tol = tol; P.tol_cg = o.tol_cg > 0.0 ? o.tol_cg : tol;
+  P.max_mm = o.max_mm; P.max_cg = o.max_cg; P.min_cg = o.min_cg;
+  P.S = h->bS; P.kchunk = h->bkchunk;
+  double** v = h->bvec;
+  P.x = v[0]; P.r = v[1]; P.z = v[2]; P.pb0 = v[3]; P.pb1 = v[4]; P.q = v[5]; P.la = v[6];
+  P.wl = v[7]; P.wr = v[8]; P.wu = v[9]; P.wd = v[10]; P.idg = v[11]; P.t0 = v[12];
+  P.Ps = h->Ps; P.Us = h->Us; P.Upart = h->Upart; P.U0part = h->U0part; P.U0 = h->U0;
+  P.red = h->bred;
+  P.bar = reinterpret_cast<unsigned*>(h->bctl);
+  P.err = reinterpret_cast<int*>(h->bctl + 64);
+  P.stats = h->bstats;
+  P.timeout = o.wait_cycles > 0 ? o.wait_cycles : (1LL << 33);
+  const size_t smem = batch_smem_bytes(NR);
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
+  FLR_TRY(cudaFuncSetAttribute(mm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int nb = 0;
+  FLR_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mm_batch_kernel, kBT, smem));
+  if (nb < 1) return FLR_ENOTIMPL;
+  const long long ntiles = (p + kTM - 1) / kTM;
+  const long long mtiles = (n + kTM - 1) / kTM;
+  long long G = std::max<long long>(ntiles, mtiles * h->bS);
+  G = std::max<long long>(1, std::min<long long>({G, (long long)h->sm_count * nb, (long long)h->sm_count}));
+  void* args[] = {(void*)&P};
+  FLR_TRY(cudaEventRecord(h->ev0, h->stream));
+  FLR_TRY(cudaLaunchCooperativeKernel((const void*)mm_batch_kernel, dim3((unsigned)G), dim3(kBT), args,
+                                      smem, h->stream));
+  FLR_TRY(cudaEventRecord(h->ev1, h->stream));
+  std::vector<BatchStats> hs((size_t)K);
+  unsigned char hctl[256];
+  FLR_TRY(cudaMemcpyAsync(hs.data(), h->bstats, sizeof(BatchStats) * K, cudaMemcpyDeviceToHost, h->stream));
+  FLR_TRY(cudaMemcpyAsync(hctl, h->bctl, 256, cudaMemcpyDeviceToHost, h->stream));
+  std::vector<double> hb((size_t)K * p);
+  FLR_TRY(cudaMemcpyAsync(hb.data(), P.x, sizeof(double) * K * p, cudaMemcpyDeviceToHost, h->stream));
+  FLR_TRY(cudaStreamSynchronize(h->stream));
+  FLR_TRY(cudaMemcpy(betas, hb.data(), sizeof(double) * K * p,
+                     io_mem == FLR_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  int herr;
+  std::memcpy(&herr, hctl + 64, sizeof(int));
+  flr_status first = FLR_OK;
+  const long long q2 = P.q2;
+  for (int k = 0; k < K; ++k) {
+    flr_status sk = herr != DERR_NONE ? FLR_ETIMEOUT
+                    : hs[k].status == -1 ? FLR_ECUDA : (flr_status)hs[k].status;
+    // f_eps = f - lam1 sum eps log(1+|b|/eps) - lam2 sum_E eps log(1+|d|/eps)  (Eq. pert)
+    const double* bk = hb.data() + (size_t)k * p;
+    double g1 = 0.0, g2 = 0.0;
+    for (long long j = 0; j < p; ++j) {
+      g1 += eps * std::log1p(std::fabs(bk[j]) / eps);
+      if ((j % q2) != q2 - 1 && j + 1 < p) g2 += eps * std::log1p(std::fabs(bk[j] - bk[j + 1]) / eps);
+      if (j + q2 < p) g2 += eps * std::log1p(std::fabs(bk[j] - bk[j + q2]) / eps);
+    }
+    if (objectives) objectives[k] = hs[k].f;
+    if (stats) {
+      stats[k].mm_iters = hs[k].mm_iters;
+      stats[k].cg_iters = hs[k].cg_iters;
+      stats[k].status = sk;
+      stats[k].grid = (int)G;
+      stats[k].f = hs[k].f;
+      stats[k].f_eps = hs[k].f - l1[k] * g1 - l2[k] * g2;
+      stats[k].rel_change = hs[k].rel_change;
+      stats[k].cg_relres = hs[k].cg_relres;
+      stats[k].ms = ms;
+    }
+    if (sk != FLR_OK && first == FLR_OK) first = sk;
+  }
+  return first;
 }
 
 }  // namespace
@@ -471,6 +617,29 @@ flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const doub
                            double eps, double tol, const flr_opts* opts, double* betas,
                            int32_t io_mem, double* objectives, flr_stats* stats) {
   if (!h || K < 0 || (K > 0 && (!lambda1 || !lambda2 || !betas))) return FLR_EINVAL;
+  if (!(eps > 0.0) || !(tol > 0.0) || (io_mem != FLR_MEM_DEVICE && io_mem != FLR_MEM_HOST)) return FLR_EINVAL;
+  for (int k = 0; k < K; ++k)
+    if (!(lambda1[k] >= 0.0) || !(lambda2[k] >= 0.0) || !std::isfinite(lambda1[k]) ||
+        !std::isfinite(lambda2[k]))
+      return FLR_EINVAL;
+  flr_opts o;
+  flr_default_opts(&o);
+  if (opts) o = *opts;
+  // tensor-core multi-RHS path: BF16 X, chain/lattice, Jacobi preconditioner
+  const bool tc_path = h->dtype == FLR_BF16 && h->gkind != FLR_E_EDGES &&
+                       (o.precond == FLR_PC_AUTO || o.precond == FLR_PC_JACOBI) && K >= 1;
+  if (tc_path) {
+    flr_status first = FLR_OK;
+    for (int k0 = 0; k0 < K; k0 += kNRMax) {
+      const int kg = std::min(kNRMax, K - k0);
+      flr_status s = batch_group(h, kg, lambda1 + k0, lambda2 + k0, eps, tol, o,
+                                 betas + (size_t)k0 * h->p, io_mem,
+                                 objectives ? objectives + k0 : nullptr, stats ? stats + k0 : nullptr);
+      if (s == FLR_EINVAL || s == FLR_ECUDA || s == FLR_ENOMEM || s == FLR_ENOTIMPL) return s;
+      if (s != FLR_OK && first == FLR_OK) first = s;
+    }
+    return first;
+  }
   flr_status first = FLR_OK;
   for (int k = 0; k < K; ++k) {
     flr_stats st{};

@@ -1,0 +1,626 @@
+// Batched MM solve: K (lambda1_k, lambda2_k) problems on the same X, y, E in
+// one persistent cooperative launch.  Each right-hand side follows the MM
+// iteration of Section 3 (reweighting, Eq. lin-sys) with PCG inner solves
+// (Algorithm 2); all K run in lockstep and a converged one is masked out.
+//
+// Per CG iteration the two X contractions of the K Q-applies are GEMMs on
+// the tensor cores (tcgen05, FP32 accumulation in TMEM):
+//   phase A  U = X P      M = n (128-row tiles), N = K, reduction over p, split
+//                         into S chunks per row tile; partial tiles are summed
+//   phase C  T = X^T U    M = p (128-column tiles), N = K, reduction over n
+// P and U are FP64/FP32 values split into three BF16 slices (hi + mid + lo,
+// 24 significant bits), so each product carries FP32-level accuracy.  X is
+// BF16 (exact).  The per-RHS vector work (Laplacian, updates, Jacobi
+// preconditioner, inner products) is FP64 on the CUDA cores, and every MM
+// iteration restarts from an FP64 residual c - X^T X b - S b and objective
+// computed on the CUDA cores (FP64 refinement).
+//
+// Work layout: 128-column tiles are owned round-robin by blocks (tile t by
+// block t mod G); a block owns the per-RHS coefficients of its tiles.  Row
+// slices of n are reduced block-wise.  Scalar reductions over blocks are FP64
+// atomics into rotating slots followed by one grid barrier.
+#pragma once
+#include "flr_device.cuh"
+#include "flr_tc.cuh"
+
+namespace flr {
+
+constexpr int kBT = 256;                 // threads per block
+constexpr int kNRMax = 64;               // right-hand sides per launch
+constexpr int kTM = 128;                 // tile rows (MMA M)
+constexpr int kNS = 3;                   // cp.async / MMA pipeline stages
+constexpr int kSlices = 3;               // BF16 slices per FP64/FP32 operand
+constexpr int kRedSlots = 3;
+
+struct BatchStats {
+  int mm_iters, cg_iters, status, pad;
+  double f, f_eps, rel_change, cg_relres;
+};
+
+struct BatchParams {
+  const __nv_bfloat16* Xr;     // row-major n x ldp
+  const __nv_bfloat16* Xt;     // column-major p x ldn
+  long long n, p, ldp, ldn, q2;
+  int K, NR;                   // problems; NR = K padded to 32 or 64 (MMA N)
+  const double* y;
+  const double* c;
+  const double* d;
+  double cnorm;
+  const double* lam1;          // K values (device)
+  const double* lam2;
+  double eps, tol, tol_cg;
+  int max_mm, max_cg, min_cg;
+  int S;                       // split-K chunks per row tile in phase A
+  long long kchunk;            // columns per split-K chunk (multiple of 64)
+  // per-RHS FP64 state, layout [k][j]
+  double *x, *r, *z, *pb0, *pb1, *q, *la, *wl, *wr, *wu, *wd, *idg, *t0;
+  __nv_bfloat16* Ps;           // [3][NR][ldp]
+  __nv_bfloat16* Us;           // [3][NR][ldn]
+  float* Upart;                // [S][NR][n]
+  double* U0part;              // [S][NR][n]
+  double* U0;                  // [NR][n]
+  double* red;                 // [kRedSlots][4*kNRMax]
+  unsigned* bar;
+  int* err;
+  BatchStats* stats;           // K entries
+  long long timeout;
+};
+
+__host__ __device__ inline size_t batch_smem_bytes(int NR) {
+  const size_t stage = (size_t)kTM * tc::kTileBytesPerRow + (size_t)kSlices * NR * tc::kTileBytesPerRow;
+  return kNS * stage                     // operand pipeline
+         + (size_t)kNRMax * kTM * 4      // staged accumulator tile (floats)
+         + (size_t)64 * kNRMax * 8       // FP64 operand chunk of the refinement passes
+         + 32 * (size_t)kNRMax * 8       // per-RHS scalars
+         + 256;
+}
+
+__device__ __forceinline__ void split3(double v, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __double2bfloat16(v);
+  const double r1 = v - (double)__bfloat162float(h);
+  m = __double2bfloat16(r1);
+  const double r2 = r1 - (double)__bfloat162float(m);
+  l = __double2bfloat16(r2);
+}
+
+// D(tmem, 128 x NR, f32) = A[128 x klen] * (B0 + B1 + B2)[NR x klen]^T
+// A row r (r < a_rows, else zero) at A + r*lda + kA0; B slice s row k at
+// B + s*bs + k*ldb + kB0.  Columns at or beyond kvalid (relative to the row
+// start) are zero.  All threads call; thread 0 issues the MMAs.
+struct TcPipe {
+  unsigned char* st;     // kNS stages
+  uint64_t* mbar;        // kNS mbarriers
+  uint32_t phase;        // bit s = parity of stage s's next completion
+  uint32_t tmem;
+  long long timeout;
+  int* err;
+};
+
+__device__ __forceinline__ bool tc_tile(TcPipe& tp, const __nv_bfloat16* A, long long lda,
+                                        int a_rows, long long kA0, long long a_kvalid,
+                                        const __nv_bfloat16* B, long long ldb, long long bs,
+                                        long long kB0, long long b_kvalid, long long klen, int NR) {
+  using namespace tc;
+  const int tid = threadIdx.x;
+  const size_t a_bytes = (size_t)kTM * kTileBytesPerRow;
+  const size_t b_bytes = (size_t)NR * kTileBytesPerRow;
+  const size_t stage_bytes = a_bytes + kSlices * b_bytes;
+  const int nch = (int)((klen + KC - 1) / KC);
+  const uint32_t idesc = idesc_bf16(kTM, NR);
+  auto load = [&](int ch) {
+    unsigned char* sb = tp.st + (size_t)(ch % kNS) * stage_bytes;
+    const long long k0 = (long long)ch * KC;
+    const int a_chunks = kTM * (KC / 8);
+    const int b_chunks = kSlices * NR * (KC / 8);
+    for (int cidx = tid; cidx < a_chunks + b_chunks; cidx += kBT) {
+      if (cidx < a_chunks) {
+        const int r = cidx >> 3, kb = cidx & 7;
+        const long long kk = kA0 + k0 + kb * 8;
+        const bool ok = r < a_rows && (k0 + kb * 8 < klen) && kk + 8 <= a_kvalid;
+        const __nv_bfloat16* src = ok ? A + (long long)r * lda + kk : A;
+        cp_async16(sb + tile_off(r, kb * 8), src, ok);
+      } else {
+        const int c2 = cidx - a_chunks;
+        const int s = c2 / (NR * 8), rem = c2 % (NR * 8);
+        const int r = rem >> 3, kb = rem & 7;
+        const long long kk = kB0 + k0 + kb * 8;
+        const bool ok = (k0 + kb * 8 < klen) && kk + 8 <= b_kvalid;
+        const __nv_bfloat16* src = ok ? B + (long long)s * bs + (long long)r * ldb + kk : B;
+        cp_async16(sb + a_bytes + (size_t)s * b_bytes + tile_off(r, kb * 8), src, ok);
+      }
+    }
+  };
+  bool ok = true;
+  for (int ch = 0; ch < kNS - 1; ++ch) {
+    if (ch < nch) load(ch);
+    cp_async_commit();
+  }
+  for (int ch = 0; ch < nch; ++ch) {
+    const int nxt = ch + kNS - 1;
+    if (nxt < nch) {
+      const int s = nxt % kNS;
+      if (nxt >= kNS) {   // stage s was last used by chunk nxt - kNS: wait for its MMAs
+        if (ok && !mbar_wait(&tp.mbar[s], (tp.phase >> s) & 1u, tp.timeout)) ok = false;
+        tp.phase ^= 1u << s;
+      }
+      load(nxt);
+    }
+    cp_async_commit();
+    cp_async_wait<kNS - 1>();
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0 && ok) {
+      fence_after();
+      const unsigned char* sb = tp.st + (size_t)(ch % kNS) * stage_bytes;
+      const uint32_t a0 = smem_u32(sb);
+      for (int ks = 0; ks < KC / 16; ++ks) {
+        for (int s = 0; s < kSlices; ++s) {
+          const uint32_t b0 = smem_u32(sb + a_bytes + (size_t)s * b_bytes);
+          mma_bf16(tp.tmem, desc(a0 + ks * 2 * kLBO), desc(b0 + ks * 2 * kLBO), idesc,
+                   (ch > 0 || ks > 0 || s > 0) ? 1u : 0u);
+        }
+      }
+      commit(&tp.mbar[ch % kNS]);
+    }
+  }
+  // drain: wait for the outstanding commits (the last min(nch, kNS) chunks)
+  for (int ch = nch - (nch < kNS ? nch : kNS); ch < nch; ++ch) {
+    const int s = ch % kNS;
+    if (ok && !mbar_wait(&tp.mbar[s], (tp.phase >> s) & 1u, tp.timeout)) ok = false;
+    tp.phase ^= 1u << s;
+  }
+  fence_after();
+  ok = __syncthreads_and(ok ? 1 : 0) != 0;   // one outcome for the whole block
+  if (!ok && tid == 0) atomicCAS(tp.err, DERR_NONE, DERR_TIMEOUT);
+  return ok;
+}
+
+// Copy the 128 x NR accumulator tile out of TMEM into shared memory as
+// ts[k][row] (floats).  Warps w and w+4 share TMEM lanes 32(w%4)..+31.
+__device__ __forceinline__ void tmem_to_smem(uint32_t tmem, float* ts, int NR) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane_base = (warp & 3) * 32;
+  const int half = NR / 2;
+  const int c_begin = (warp < 4) ? 0 : half;
+  for (int c0 = c_begin; c0 < c_begin + half; c0 += 16) {
+    float v[16];
+    tc::tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)c0, v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) ts[(c0 + i) * kTM + lane_base + lane] = v[i];
+  }
+  tc::fence_before();
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
+  extern __shared__ __align__(1024) unsigned char smb[];
+  const int tid = threadIdx.x;
+  const int G = gridDim.x, b = blockIdx.x;
+  const long long n = P.n, p = P.p, q2 = P.q2;
+  const int K = P.K, NR = P.NR;
+  const long long ntiles = (p + kTM - 1) / kTM;
+  const long long mtiles = (n + kTM - 1) / kTM;
+
+  const size_t stage_bytes = (size_t)kTM * tc::kTileBytesPerRow + (size_t)kSlices * NR * tc::kTileBytesPerRow;
+  unsigned char* stages = smb;
+  float* ts = reinterpret_cast<float*>(smb + kNS * stage_bytes);            // [NR][128]
+  double* b64 = reinterpret_cast<double*>(ts + kNRMax * kTM);              // [64][kNRMax]
+  double* scal = b64 + 64 * kNRMax;                                         // per-RHS scalars
+  double* s_rz = scal;                 double* s_rr = scal + kNRMax;
+  double* s_nu = scal + 2 * kNRMax;    double* s_gam = scal + 3 * kNRMax;
+  double* s_f = scal + 4 * kNRMax;     double* s_fp = scal + 5 * kNRMax;
+  double* s_rel = scal + 6 * kNRMax;   double* s_rss = scal + 7 * kNRMax;
+  double* s_relres = scal + 8 * kNRMax; double* s_pen = scal + 9 * kNRMax;   // 2 * kNRMax
+  double* s_psp = scal + 11 * kNRMax;  double* s_uu = scal + 12 * kNRMax;
+  int* s_act = reinterpret_cast<int*>(scal + 13 * kNRMax);      // MM-active
+  int* s_cga = s_act + kNRMax;                                     // CG-active
+  int* s_mm = s_act + 2 * kNRMax;
+  int* s_cg = s_act + 3 * kNRMax;
+  int* s_st = s_act + 4 * kNRMax;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(scal + 32 * kNRMax);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kNS);
+
+  GridBarrier gb{P.bar, P.err, 0u, P.timeout};
+  int redi = 0;
+  // grid sum of nf fields (per-block partials in `loc` of thread t for field t)
+  auto grid_red = [&](double* out, const double* loc_smem, int nf) -> bool {
+    double* slot = P.red + (size_t)(redi % kRedSlots) * 4 * kNRMax;
+    for (int f = tid; f < nf; f += kBT) atomicAdd(slot + f, loc_smem[f]);
+    if (!gb.sync()) return false;
+    for (int f = tid; f < nf; f += kBT) out[f] = ldcg(slot + f);
+    if (b == 0) {   // zero the slot two reductions ahead (its last reads are done)
+      double* z2 = P.red + (size_t)((redi + 2) % kRedSlots) * 4 * kNRMax;
+      for (int f = tid; f < 4 * kNRMax; f += kBT) z2[f] = 0.0;
+    }
+    ++redi;
+    __syncthreads();
+    return true;
+  };
+
+  // ---- TMEM, mbarriers
+  if ((tid >> 5) == 0) tc::tmem_alloc(tslot, 64);
+  if (tid == 0) {
+    for (int s = 0; s < kNS; ++s) tc::mbar_init(&mbar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  TcPipe tp{stages, mbar, 0u, tslot[0], P.timeout, P.err};
+
+  // ---- initialisation (Algorithm 1) for every RHS
+  for (long long t = b; t < ntiles; t += G)
+    for (int e = tid; e < K * kTM; e += kBT) {
+      const int k = e / kTM;
+      const long long j = t * kTM + (e % kTM);
+      if (j < p) P.x[(long long)k * p + j] = P.d[j] != 0.0 ? P.c[j] / P.d[j] : 0.0;
+    }
+  for (int k = tid; k < kNRMax; k += kBT) {
+    s_act[k] = k < K ? 1 : 0; s_cga[k] = 0; s_mm[k] = 0; s_cg[k] = 0; s_st[k] = 0;
+    s_f[k] = 0.0; s_fp[k] = 0.0; s_rel[k] = 0.0; s_relres[k] = 0.0;
+  }
+  bool alive = gb.sync();
+  int mm = 0, pcur = 0;
+  auto is_own = [&](long long j) -> bool { return ((j / kTM) % G) == b; };
+
+  while (alive) {
+    // ---------------- reweight (Eq. lin-sys) per active RHS; S x; penalties
+    for (int f = tid; f < 2 * kNRMax; f += kBT) s_pen[f] = 0.0;
+    __syncthreads();
+    for (long long t = b; t < ntiles; t += G) {
+      for (int e = tid; e < K * kTM; e += kBT) {
+        const int k = e / kTM;
+        if (!s_act[k]) continue;
+        const long long j = t * kTM + (e % kTM);
+        if (j >= p) continue;
+        const double* xk = P.x + (long long)k * p;
+        const double xj = ldcg(xk + j);
+        const double l1 = P.lam1[k], l2 = P.lam2[k];
+        const long long col = j % q2;
+        double wl_ = 0.0, wr_ = 0.0, wu_ = 0.0, wd_ = 0.0, lap = 0.0, pen2 = 0.0;
+        if (col != 0) { const double v = ldcg(xk + j - 1); wl_ = 1.0 / (fabs(v - xj) + P.eps); lap = fma(wl_, xj - v, lap); }
+        if (col != q2 - 1 && j + 1 < p) { const double v = ldcg(xk + j + 1); wr_ = 1.0 / (fabs(xj - v) + P.eps); lap = fma(wr_, xj - v, lap); pen2 += fabs(xj - v); }
+        if (j >= q2) { const double v = ldcg(xk + j - q2); wu_ = 1.0 / (fabs(v - xj) + P.eps); lap = fma(wu_, xj - v, lap); }
+        if (j + q2 < p) { const double v = ldcg(xk + j + q2); wd_ = 1.0 / (fabs(xj - v) + P.eps); lap = fma(wd_, xj - v, lap); pen2 += fabs(xj - v); }
+        const long long o = (long long)k * p + j;
+        const double la = l1 / (fabs(xj) + P.eps);
+        P.la[o] = la;
+        P.wl[o] = l2 * wl_; P.wr[o] = l2 * wr_; P.wu[o] = l2 * wu_; P.wd[o] = l2 * wd_;
+        const double deg = (wl_ + wr_) + (wu_ + wd_);
+        P.idg[o] = 1.0 / fma(l2, deg, la + P.d[j]);
+        P.q[o] = fma(la, xj, l2 * lap);
+        atomicAdd(&s_pen[k], fabs(xj));
+        if (pen2 != 0.0) atomicAdd(&s_pen[kNRMax + k], pen2);
+      }
+    }
+    // ---------------- FP64 refinement pass 1: U0 = X b (CUDA cores, FP64)
+    for (long long it = b; it < mtiles * P.S; it += G) {
+      const long long mt = it % mtiles, sp = it / mtiles;
+      const long long jb = sp * P.kchunk, je = jb + P.kchunk < p ? jb + P.kchunk : p;
+      const int row = tid % kTM, h = tid / kTM;       // 2 halves of 32 RHS
+      const long long i = mt * kTM + row;
+      double acc[32];
+#pragma unroll
+      for (int m = 0; m < 32; ++m) acc[m] = 0.0;
+      for (long long j0 = jb; j0 < je; j0 += 64) {
+        __syncthreads();
+        for (int e = tid; e < 64 * kNRMax; e += kBT) {
+          const int jj = e / kNRMax, k = e % kNRMax;
+          const long long j = j0 + jj;
+          b64[jj * kNRMax + k] = (k < K && s_act[k] && j < je) ? ldcg(P.x + (long long)k * p + j) : 0.0;
+        }
+        __syncthreads();
+        const int jn = (int)(je - j0 < 64 ? je - j0 : 64);
+        if (i < n) {
+          for (int jj = 0; jj < jn; ++jj) {
+            const double xv = (double)__bfloat162float(P.Xt[(j0 + jj) * P.ldn + i]);
+            const double* bb = b64 + jj * kNRMax + h * 32;
+#pragma unroll
+            for (int m = 0; m < 32; ++m) acc[m] = fma(xv, bb[m], acc[m]);
+          }
+        }
+      }
+      if (i < n) {
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+          const int k = h * 32 + m;
+          if (k < NR) P.U0part[((long long)sp * NR + k) * n + i] = acc[m];
+        }
+      }
+    }
+    __syncthreads();
+    if (!grid_red(s_pen, s_pen, 2 * kNRMax)) { alive = false; break; }
+    // ---------------- reduce U0 over the split chunks; residual sum of squares
+    for (int f = tid; f < kNRMax; f += kBT) s_rss[f] = 0.0;
+    __syncthreads();
+    {
+      const long long rows_per = (n + G - 1) / G;
+      const long long i0 = (long long)b * rows_per, i1 = i0 + rows_per < n ? i0 + rows_per : n;
+      for (long long e = tid; e < (long long)K * (i1 > i0 ? i1 - i0 : 0); e += kBT) {
+        const int k = (int)(e / (i1 - i0));
+        const long long i = i0 + e % (i1 - i0);
+        if (!s_act[k]) continue;
+        double s = 0.0;
+        for (int sp = 0; sp < P.S; ++sp) s += ldcg(P.U0part + ((long long)sp * NR + k) * n + i);
+        P.U0[(long long)k * n + i] = s;
+        const double rr = P.y[i] - s;
+        atomicAdd(&s_rss[k], rr * rr);
+      }
+    }
+    __syncthreads();
+    if (!grid_red(s_rss, s_rss, kNRMax)) { alive = false; break; }
+    // ---------------- objective f(beta_k) (Eq. obj) and the outer stop per RHS
+    if (tid < K) {
+      const int k = tid;
+      if (s_act[k]) {
+        const double fk = 0.5 * s_rss[k] + P.lam1[k] * s_pen[k] + P.lam2[k] * s_pen[kNRMax + k];
+        s_f[k] = fk;
+        if (!isfinite(fk)) { s_act[k] = 0; s_st[k] = ST_NONFINITE; }
+        else if (s_mm[k] > 0) {
+          s_rel[k] = fabs(fk - s_fp[k]) / fabs(s_fp[k]);
+          if (s_rel[k] <= P.tol) s_act[k] = 0;
+        }
+        if (s_act[k] && s_mm[k] >= P.max_mm) { s_act[k] = 0; s_st[k] = ST_NOTCONV; }
+      }
+    }
+    __syncthreads();
+    int nact = 0;
+    for (int k = 0; k < K; ++k) nact += s_act[k];
+    if (nact == 0) break;
+    // ---------------- FP64 refinement pass 2: r0 = c - X^T U0 - S b; z0; p1 = z0
+    for (int f = tid; f < kNRMax; f += kBT) { s_rz[f] = 0.0; s_rr[f] = 0.0; }
+    __syncthreads();
+    for (long long t = b; t < ntiles; t += G) {
+      const int cl = tid % kTM, h = tid / kTM;
+      const long long j = t * kTM + cl;
+      double acc[32];
+#pragma unroll
+      for (int m = 0; m < 32; ++m) acc[m] = 0.0;
+      for (long long i0 = 0; i0 < n; i0 += 64) {
+        __syncthreads();
+        for (int e = tid; e < 64 * kNRMax; e += kBT) {
+          const int ii = e / kNRMax, k = e % kNRMax;
+          const long long i = i0 + ii;
+          b64[ii * kNRMax + k] = (k < K && s_act[k] && i < n) ? ldcg(P.U0 + (long long)k * n + i) : 0.0;
+        }
+        __syncthreads();
+        const int in = (int)(n - i0 < 64 ? n - i0 : 64);
+        if (j < p) {
+          for (int ii = 0; ii < in; ++ii) {
+            const double xv = (double)__bfloat162float(P.Xt[j * P.ldn + i0 + ii]);
+            const double* bb = b64 + ii * kNRMax + h * 32;
+#pragma unroll
+            for (int m = 0; m < 32; ++m) acc[m] = fma(xv, bb[m], acc[m]);
+          }
+        }
+      }
+      if (j < p) {
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+          const int k = h * 32 + m;
+          if (k < K && s_act[k]) P.t0[(long long)k * p + j] = acc[m];
+        }
+      }
+    }
+    __syncthreads();
+    {
+      double* pc = pcur ? P.pb1 : P.pb0;
+      for (long long t = b; t < ntiles; t += G) {
+        for (int e = tid; e < K * kTM; e += kBT) {
+          const int k = e / kTM;
+          const long long j = t * kTM + (e % kTM);
+          if (j >= p || !s_act[k]) continue;
+          const long long o = (long long)k * p + j;
+          const double rj = (P.c[j] - P.t0[o]) - P.q[o];
+          const double zj = rj * P.idg[o];
+          P.r[o] = rj; P.z[o] = zj; pc[o] = zj;
+          atomicAdd(&s_rz[k], rj * zj);
+          atomicAdd(&s_rr[k], rj * rj);
+        }
+      }
+    }
+    __syncthreads();
+    // rz and rr as one 2*kNRMax-field reduction
+    {
+      double* tmp = s_nu;   // s_nu, s_gam are adjacent: 2*kNRMax doubles
+      for (int f = tid; f < kNRMax; f += kBT) { tmp[f] = s_rz[f]; tmp[kNRMax + f] = s_rr[f]; }
+      __syncthreads();
+      if (!grid_red(tmp, tmp, 2 * kNRMax)) { alive = false; break; }
+      for (int f = tid; f < kNRMax; f += kBT) { s_rz[f] = tmp[f]; s_rr[f] = tmp[kNRMax + f]; s_gam[f] = 0.0; }
+    }
+    if (tid < kNRMax) s_cga[tid] = (tid < K && s_act[tid]) ? 1 : 0;
+    __syncthreads();
+    // ---------------- CG iterations for all active RHS
+    int kcg = 0;
+    while (true) {
+      if (tid < K) {
+        const int k = tid;
+        if (s_cga[k]) {
+          const double rel_r = sqrt(s_rr[k]) / P.cnorm;
+          s_relres[k] = rel_r;
+          if (kcg >= P.max_cg || (kcg >= P.min_cg && rel_r <= P.tol_cg)) s_cga[k] = 0;
+          else s_cg[k] += 1;
+        }
+      }
+      __syncthreads();
+      int ncga = 0;
+      for (int k = 0; k < K; ++k) ncga += s_cga[k];
+      if (ncga == 0) break;
+      const double* pc = pcur ? P.pb1 : P.pb0;
+      const double* po = pcur ? P.pb0 : P.pb1;
+      // (a) S p, p^T S p, and the BF16 slices of p for the owned columns
+      for (int f = tid; f < kNRMax; f += kBT) s_psp[f] = 0.0;
+      __syncthreads();
+      for (long long t = b; t < ntiles; t += G) {
+        for (int e = tid; e < NR * kTM; e += kBT) {
+          const int k = e / kTM;
+          const long long j = t * kTM + (e % kTM);
+          if (j >= p) continue;
+          const long long o = (long long)k * p + j;
+          __nv_bfloat16 h = __float2bfloat16(0.f), m = h, l = h;
+          if (k < K && s_cga[k]) {
+            const double g = s_gam[k];
+            auto pv = [&](long long kk) -> double {
+              const long long ok = (long long)k * p + kk;
+              if (is_own(kk)) return pc[ok];
+              if (kcg == 0) return ldcg(pc + ok);
+              return fma(g, ldcg(po + ok), ldcg(P.z + ok));
+            };
+            const double pj = pc[o];
+            const long long col = j % q2;
+            double lap = 0.0;
+            if (col != 0) lap = fma(P.wl[o], pj - pv(j - 1), lap);
+            if (col != q2 - 1 && j + 1 < p) lap = fma(P.wr[o], pj - pv(j + 1), lap);
+            if (j >= q2) lap = fma(P.wu[o], pj - pv(j - q2), lap);
+            if (j + q2 < p) lap = fma(P.wd[o], pj - pv(j + q2), lap);
+            const double spj = fma(P.la[o], pj, lap);
+            P.q[o] = spj;
+            atomicAdd(&s_psp[k], pj * spj);
+            split3(pj, h, m, l);
+          }
+          P.Ps[(0LL * NR + k) * P.ldp + j] = h;
+          P.Ps[(1LL * NR + k) * P.ldp + j] = m;
+          P.Ps[(2LL * NR + k) * P.ldp + j] = l;
+        }
+      }
+      __syncthreads();
+      if (!grid_red(s_psp, s_psp, kNRMax)) { alive = false; break; }
+      // (b) phase A: U partials = X[rows, chunk] P[chunk]  (tensor cores)
+      for (long long it = b; it < mtiles * P.S; it += G) {
+        const long long mt = it % mtiles, sp = it / mtiles;
+        const long long jb = sp * P.kchunk;
+        const long long klen = jb + P.kchunk < P.ldp ? P.kchunk : P.ldp - jb;
+        if (klen <= 0) continue;
+        const int rows = (int)(n - mt * kTM < kTM ? n - mt * kTM : kTM);
+        if (!tc_tile(tp, P.Xr + mt * kTM * P.ldp, P.ldp, rows, jb, P.ldp, P.Ps, P.ldp,
+                     (long long)NR * P.ldp, jb, P.ldp, klen, NR)) { alive = false; break; }
+        tmem_to_smem(tp.tmem, ts, NR);
+        for (int e = tid; e < NR * kTM; e += kBT) {
+          const int k = e / kTM, rr = e % kTM;
+          const long long i = mt * kTM + rr;
+          if (i < n) P.Upart[((long long)sp * NR + k) * n + i] = ts[k * kTM + rr];
+        }
+        __syncthreads();
+      }
+      if (!alive) break;
+      if (!gb.sync()) { alive = false; break; }
+      // (c) U = sum of partials; ||U_k||^2; BF16 slices of U
+      for (int f = tid; f < kNRMax; f += kBT) s_uu[f] = 0.0;
+      __syncthreads();
+      {
+        const long long rows_per = (P.ldn + G - 1) / G;
+        const long long i0 = (long long)b * rows_per;
+        const long long i1 = i0 + rows_per < P.ldn ? i0 + rows_per : P.ldn;
+        const long long cnt = i1 > i0 ? i1 - i0 : 0;
+        for (long long e = tid; e < (long long)NR * cnt; e += kBT) {
+          const int k = (int)(e / cnt);
+          const long long i = i0 + e % cnt;
+          double s = 0.0;
+          if (i < n && k < K && s_cga[k])
+            for (int sp = 0; sp < P.S; ++sp) s += (double)ldcg(P.Upart + ((long long)sp * NR + k) * n + i);
+          __nv_bfloat16 h, m, l;
+          split3(s, h, m, l);
+          P.Us[(0LL * NR + k) * P.ldn + i] = h;
+          P.Us[(1LL * NR + k) * P.ldn + i] = m;
+          P.Us[(2LL * NR + k) * P.ldn + i] = l;
+          if (s != 0.0) atomicAdd(&s_uu[k], s * s);
+        }
+      }
+      __syncthreads();
+      if (!grid_red(s_uu, s_uu, kNRMax)) { alive = false; break; }
+      if (tid < K) {
+        const int k = tid;
+        double nu = 0.0;
+        if (s_cga[k]) {
+          const double pq = s_uu[k] + s_psp[k];
+          if (!(pq > 0.0) || !isfinite(pq)) {
+            s_cga[k] = 0; s_act[k] = 0; s_st[k] = isfinite(pq) ? ST_BREAKDOWN : ST_NONFINITE;
+          } else {
+            nu = s_rz[k] / pq;
+          }
+        }
+        s_nu[k] = nu;
+      }
+      __syncthreads();
+      // (d) phase C: T = X^T U for the owned tiles (tensor cores), then the updates
+      double* loc = s_pen;   // 2*kNRMax partials: r^T z, r^T r
+      for (int f = tid; f < 2 * kNRMax; f += kBT) loc[f] = 0.0;
+      __syncthreads();
+      for (long long t = b; t < ntiles; t += G) {
+        const int rows = (int)(p - t * kTM < kTM ? p - t * kTM : kTM);
+        if (!tc_tile(tp, P.Xt + t * kTM * P.ldn, P.ldn, rows, 0, P.ldn, P.Us, P.ldn,
+                     (long long)NR * P.ldn, 0, P.ldn, P.ldn, NR)) { alive = false; break; }
+        tmem_to_smem(tp.tmem, ts, NR);
+        for (int e = tid; e < K * kTM; e += kBT) {
+          const int k = e / kTM, cl = e % kTM;
+          const long long j = t * kTM + cl;
+          if (j >= p || !s_cga[k]) continue;
+          const long long o = (long long)k * p + j;
+          const double nu = s_nu[k];
+          const double qj = (double)ts[k * kTM + cl] + P.q[o];
+          P.x[o] = fma(nu, pc[o], P.x[o]);
+          const double rj = fma(-nu, qj, P.r[o]);
+          const double zj = rj * P.idg[o];
+          P.r[o] = rj;
+          P.z[o] = zj;
+          atomicAdd(&loc[k], rj * zj);
+          atomicAdd(&loc[kNRMax + k], rj * rj);
+        }
+        __syncthreads();
+      }
+      if (!alive) break;
+      if (!grid_red(loc, loc, 2 * kNRMax)) { alive = false; break; }
+      // (e) gamma_k and p_{j+1} = z + gamma p
+      if (tid < K) {
+        const int k = tid;
+        if (s_cga[k]) {
+          s_gam[k] = loc[k] / s_rz[k];
+          s_rz[k] = loc[k];
+          s_rr[k] = loc[kNRMax + k];
+        }
+      }
+      __syncthreads();
+      {
+        double* pn = pcur ? P.pb0 : P.pb1;
+        for (long long t = b; t < ntiles; t += G)
+          for (int e = tid; e < K * kTM; e += kBT) {
+            const int k = e / kTM;
+            const long long j = t * kTM + (e % kTM);
+            if (j >= p || !s_cga[k]) continue;
+            const long long o = (long long)k * p + j;
+            pn[o] = fma(s_gam[k], pc[o], P.z[o]);
+          }
+      }
+      pcur ^= 1;
+      ++kcg;
+      __syncthreads();
+    }
+    if (!alive) break;
+    if (tid < K) {
+      if (s_act[tid]) { s_fp[tid] = s_f[tid]; s_mm[tid] += 1; }
+    }
+    ++mm;
+    __syncthreads();
+    if (!gb.sync()) { alive = false; break; }
+  }
+
+  // ---- statistics (f_eps is left to the host)
+  if (alive && b == 0) {
+    for (int k = tid; k < K; k += kBT) {
+      BatchStats* S = P.stats + k;
+      S->mm_iters = s_mm[k];
+      S->cg_iters = s_cg[k];
+      S->status = s_st[k];
+      S->pad = 0;
+      S->f = s_f[k];
+      S->f_eps = 0.0;
+      S->rel_change = s_rel[k];
+      S->cg_relres = s_relres[k];
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if ((tid >> 5) == 0) tc::tmem_dealloc(tslot[0], 64);
+}
+
+}  // namespace flr
