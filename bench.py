@@ -40,7 +40,11 @@ def parse():
     ap.add_argument("--precond", default="jacobi")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--once", default=None, choices=["config2", "config4"],
+    ap.add_argument("--requests", type=int, default=120, help="served stream length (serve5)")
+    ap.add_argument("--served-slots", type=int, default=4,
+                    help="concurrent copies for the served-form measurement (0 = skip)")
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--once", default=None, choices=["config2", "config4", "batch3", "serve5"],
                     help="one solve of a workload (for profiler captures), then exit")
     ap.add_argument("--max-mm", type=int, default=20000)
     ap.add_argument("--max-cg", type=int, default=10000)
@@ -52,6 +56,22 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(t_local, pg=None, device=None):
+    """The slowest rank's time (every rank gets it); t_local when not distributed."""
+    if pg is None:
+        return t_local
+    import torch
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.barrier()
+    return float(t.item())
+
+
+def replica_throughput(world, steps, t_max):
+    """Whole-job solves/s: every rank solved `steps` problems within t_max."""
+    return world * steps / t_max
 
 
 def load_golden():
@@ -200,11 +220,110 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def solve_batch3(args):
+    """The 8x8 lambda grid of the batched chain workload (n=2000, p=20000, BF16 X) as one
+    flr_solve_batch call, and a few of its points as single solves for comparison."""
+    import torch
+    import flr_inputs as fi
+    import paper_1306_1970_gb300 as flr
+    flr.load(build_if_missing=True)
+    pr = fi.config(3)
+    X = torch.from_numpy(pr.X).view(torch.int16).cuda()
+    prob = flr.Problem(X, torch.from_numpy(pr.y).cuda(), pr.graph, dtype="bf16")
+    grid = pr.lam_grid
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    betas, objs, sts = prob.solve_batch(grid[:, 0], grid[:, 1], eps=pr.eps, tol=args.tol,
+                                        tol_cg=args.tol_cg, max_mm=args.max_mm, max_cg=args.max_cg,
+                                        check=False)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    out = {"once": "batch3", "K": len(grid), "seconds": tb, "kernel_ms": sts[0].ms,
+           "mm_iters": [s.mm_iters for s in sts], "cg_iters": [s.cg_iters for s in sts],
+           "status": [s.status for s in sts]}
+    single = []
+    for k in (0, 27, 63):
+        t0 = time.perf_counter()
+        _, s1 = prob.solve(grid[k, 0], grid[k, 1], eps=pr.eps, tol=args.tol, tol_cg=args.tol_cg,
+                           max_mm=args.max_mm, max_cg=args.max_cg, check=False)
+        torch.cuda.synchronize()
+        single.append({"k": k, "seconds": time.perf_counter() - t0, "mm": s1.mm_iters,
+                       "cg": s1.cg_iters, "f": s1.f, "f_batch": sts[k].f, "status": s1.status})
+    out["single"] = single
+    print(json.dumps(out))
+
+
+def serve5(args):
+    """Served mixed stream: closed loop (all requests queued at once) for the capacity,
+    then Poisson arrivals at 0.8 x capacity for p50/p99 latency (submit to done).
+    p log-uniform in [500, 5000], n = p/4, FP32 or BF16 X, chain / lattice / 5-NN."""
+    import threading
+    import torch
+    import flr_inputs as fi
+    import paper_1306_1970_gb300 as flr
+    flr.load(build_if_missing=True)
+    reqs = fi.served_stream(args.requests, seed=5000, p_lo=500, p_hi=5000)
+    data = []
+    for r in reqs:
+        pr = fi.request_problem(r)
+        X = torch.from_numpy(np.ascontiguousarray(pr.X))
+        if pr.dtype == "bf16":
+            X = X.view(torch.int16)
+        data.append((r, pr, X.pin_memory(), torch.from_numpy(pr.y).pin_memory()))
+
+    def submit(srv, item):
+        r, pr, X, y = item
+        return srv.submit(X, y, pr.graph, r.lam1, r.lam2, eps=pr.eps, tol=args.tol,
+                          dtype="bf16" if pr.dtype == "bf16" else None, tol_cg=args.tol_cg,
+                          max_mm=args.max_mm)
+
+    srv = flr.Server(slots=args.slots)
+    t0 = time.perf_counter()
+    ids = [submit(srv, it) for it in data]
+    res = [srv.wait(i)[1] for i in ids]
+    closed = time.perf_counter() - t0
+    srv.close()
+    cap = len(data) / closed
+    rate = 0.8 * cap
+    srv = flr.Server(slots=args.slots)
+    ids = [None] * len(data)
+    start = time.perf_counter()
+
+    def feeder():
+        for k, (r, it) in enumerate(zip(reqs, data)):
+            due = start + r.arrival / rate
+            dt = due - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids[k] = submit(srv, it)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    lat, statuses = [], []
+    for i in ids:
+        _, rr = srv.wait(i)
+        lat.append(rr.t_end - rr.t_submit)
+        statuses.append(rr.status)
+    opened = time.perf_counter() - start
+    srv.close()
+    print(json.dumps({"once": "serve5", "requests": len(data), "slots": args.slots,
+                      "closed_loop_fits_per_s": cap, "open_loop_rate": rate,
+                      "open_loop_fits_per_s": len(data) / opened,
+                      "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                      "status_ok": int(sum(1 for s in statuses if s == 0)),
+                      "closed_status_ok": int(sum(1 for r in res if r.status == 0))}))
+
+
 def solve_once(args):
     """One solve of a workload with capped iterations (the unit a profiler captures)."""
     import torch
     import flr_inputs as fi
     import paper_1306_1970_gb300 as flr
+    if args.once == "batch3":
+        return solve_batch3(args)
+    if args.once == "serve5":
+        return serve5(args)
     flr.load(build_if_missing=True)
     pr = fi.config(2) if args.once == "config2" else fi.config(4)
     X = torch.from_numpy(pr.X).cuda()
@@ -275,13 +394,8 @@ def main():
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_dev = sum(step_ms) / 1000.0
-    if pg:
-        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_dev = float(t.item())
-        pg.barrier()
-    value = world * args.steps / t_dev
+    t_dev = max_over_ranks(sum(step_ms) / 1000.0, pg, dev)
+    value = replica_throughput(world, args.steps, t_dev)
 
     # ---- end to end through the C ABI with host buffers: create from pinned host X, y,
     #      solve, beta back to pinned host memory, destroy -- all inside the timed region
@@ -300,12 +414,32 @@ def main():
         ph.close()
     e1.record(stream)
     torch.cuda.synchronize()
-    t_e2e = e0.elapsed_time(e1) / 1000.0
-    if pg:
-        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_value = world * e2e_steps / t_e2e
+    t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1000.0, pg, dev)
+    e2e_value = replica_throughput(world, e2e_steps, t_e2e)
+
+    # ---- served form: independent copies of the workload (seeds 1..S) solved concurrently
+    #      by the server, one slot each (slots x 38 blocks), after the timed region
+    served = None
+    if args.served_slots > 0 and rank == 0:
+        srv_probs = []
+        for s in range(1, args.served_slots + 1):
+            ps = fi.config(2, s=s)
+            srv_probs.append((ps, torch.from_numpy(ps.X).cuda(), torch.from_numpy(ps.y).cuda()))
+        srv = flr.Server(slots=args.served_slots)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids = [srv.submit(X_, y_, ps.graph, ps.lam1, ps.lam2, eps=ps.eps, tol=args.tol,
+                          precond=args.precond, tol_cg=args.tol_cg, max_mm=20000)
+               for ps, X_, y_ in srv_probs]
+        outs = [srv.wait(i)[1] for i in ids]
+        ts = time.perf_counter() - t0
+        srv.close()
+        served = {"solves_per_s": len(outs) / ts, "slots": args.served_slots,
+                  "grid_per_slot": 152 // args.served_slots, "seconds": ts,
+                  "status": [o.status for o in outs], "mm_iters": [o.stats.mm_iters for o in outs],
+                  "cg_iters": [o.stats.cg_iters for o in outs],
+                  "note": "independent copies of the workload (dataset seeds 1..slots) solved "
+                          "concurrently through flr_server; host wall clock from submit to last result"}
 
     if rank != 0:
         if pg:
@@ -354,6 +488,7 @@ def main():
                 "d2h_bytes_per_step": int(pr.p * 8)},
         "roofline": roof,
         "cpu_baseline": cpu,
+        "served_form": served,
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "wall_s_timed": t_wall,

@@ -214,6 +214,69 @@ flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n, int64_t p
                              double eps, double tol, const flr_opts* opts, double* beta_out,
                              void* stream, flr_stats* stats);
 
+
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop that keeps several FLR fits on the GPU at once.
+ * (Deployment layer; the paper solves one problem at a time.)
+ *
+ * Requests (X, y, E, lambdas) are queued by flr_server_submit.  `slots`
+ * worker threads each own a CUDA stream; a free worker admits the oldest
+ * queued request whose device-memory footprint fits in what is left of
+ * `hbm_budget`, creates its handle on the slot's stream, solves it with at
+ * most `grid_per_slot` thread blocks, copies beta to the server and frees
+ * the handle.  Requests that arrive while others run are admitted as slots
+ * and memory free up, and their kernels run concurrently on the device
+ * (slots * grid_per_slot <= number of SMs keeps every cooperative solve
+ * co-resident).  A request's X, y and edges are borrowed: they must stay
+ * valid until flr_server_wait has returned for it.
+ * ------------------------------------------------------------------------- */
+typedef struct flr_server flr_server;
+typedef flr_server* flr_server_t;
+
+typedef struct flr_server_opts {
+    int32_t slots;          /* concurrent solves (default 4) */
+    int32_t grid_per_slot;  /* thread blocks per solve (default SMs / slots) */
+    int64_t hbm_budget;     /* bytes of device memory the server may hold (default 3/4 of free) */
+    int32_t reserved[8];
+} flr_server_opts;
+
+typedef struct flr_request {
+    const void* X;          /* n x p row-major, dtype, row stride ldx (as flr_create) */
+    int32_t dtype;
+    int32_t mem;            /* FLR_MEM_HOST or FLR_MEM_DEVICE for X, y and E->edges */
+    int64_t n, p, ldx;
+    const double* y;
+    flr_graph E;
+    double lambda1, lambda2, eps, tol;
+    flr_opts opts;          /* opts.grid is capped at grid_per_slot */
+    int32_t use_opts;       /* 0: defaults */
+    int32_t reserved;
+} flr_request;
+
+typedef struct flr_result {
+    int32_t status;         /* flr_status of the solve */
+    int32_t slot;           /* worker that ran it */
+    flr_stats stats;
+    double t_submit, t_start, t_end;   /* seconds since the server was created */
+    int64_t footprint;      /* device bytes reserved for the request */
+} flr_result;
+
+/* Start a server on the current device (opts may be NULL). */
+flr_status flr_server_create(const flr_server_opts* opts, flr_server_t* out);
+/* Queue a request; FLR_EINVAL for malformed requests, FLR_ENOMEM when its
+ * footprint exceeds the whole budget (refused, never admitted). */
+flr_status flr_server_submit(flr_server_t s, const flr_request* req, uint64_t* id);
+/* 1 in *done once the request has finished. */
+flr_status flr_server_poll(flr_server_t s, uint64_t id, int32_t* done);
+/* Block until the request has finished; copies beta (p doubles, host memory;
+ * NULL to skip) and the result record, then forgets the request.  Returns the
+ * request's status; FLR_EINVAL for an unknown id. */
+flr_status flr_server_wait(flr_server_t s, uint64_t id, double* beta_out, flr_result* res);
+/* Finish every queued request, stop the workers, release the server. */
+flr_status flr_server_destroy(flr_server_t s);
+/* Device bytes flr_create + flr_solve need for a problem (admission estimate). */
+int64_t flr_footprint(int64_t n, int64_t p, int64_t m, int32_t dtype, int32_t mem);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,9 @@ DTYPE_CODES = {"f64": FLR_F64, "f32": FLR_F32, "bf16": FLR_BF16, "f16": FLR_F16}
 
 # every symbol declared in include/flr.h
 EXPORTS = ("flr_default_opts", "flr_strerror", "flr_create", "flr_solve", "flr_solve_batch",
-           "flr_destroy", "flr_get_info", "flr_solve_noalloc")
+           "flr_destroy", "flr_get_info", "flr_solve_noalloc", "flr_server_create",
+           "flr_server_submit", "flr_server_poll", "flr_server_wait", "flr_server_destroy",
+           "flr_footprint")
 
 
 class FlrGraph(ctypes.Structure):
@@ -48,6 +50,25 @@ class FlrStats(ctypes.Structure):
                 ("status", ctypes.c_int32), ("grid", ctypes.c_int32), ("f", ctypes.c_double),
                 ("f_eps", ctypes.c_double), ("rel_change", ctypes.c_double),
                 ("cg_relres", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+class FlrServerOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("grid_per_slot", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
+
+
+class FlrRequest(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("mem", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("p", ctypes.c_int64), ("ldx", ctypes.c_int64),
+                ("y", ctypes.c_void_p), ("E", FlrGraph), ("lambda1", ctypes.c_double),
+                ("lambda2", ctypes.c_double), ("eps", ctypes.c_double), ("tol", ctypes.c_double),
+                ("opts", FlrOpts), ("use_opts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class FlrResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32), ("stats", FlrStats),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_end", ctypes.c_double), ("footprint", ctypes.c_int64)]
 
 
 class FlrError(RuntimeError):
@@ -99,6 +120,18 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                       c.c_double, c.c_double, c.POINTER(FlrOpts), c.c_void_p,
                                       c.c_void_p, c.POINTER(FlrStats)]
     lib.flr_solve_noalloc.restype = c.c_int32
+    lib.flr_server_create.argtypes = [c.POINTER(FlrServerOpts), c.POINTER(c.c_void_p)]
+    lib.flr_server_create.restype = c.c_int32
+    lib.flr_server_submit.argtypes = [c.c_void_p, c.POINTER(FlrRequest), c.POINTER(c.c_uint64)]
+    lib.flr_server_submit.restype = c.c_int32
+    lib.flr_server_poll.argtypes = [c.c_void_p, c.c_uint64, c.POINTER(c.c_int32)]
+    lib.flr_server_poll.restype = c.c_int32
+    lib.flr_server_wait.argtypes = [c.c_void_p, c.c_uint64, c.c_void_p, c.POINTER(FlrResult)]
+    lib.flr_server_wait.restype = c.c_int32
+    lib.flr_server_destroy.argtypes = [c.c_void_p]
+    lib.flr_server_destroy.restype = c.c_int32
+    lib.flr_footprint.argtypes = [c.c_int64, c.c_int64, c.c_int64, c.c_int32, c.c_int32]
+    lib.flr_footprint.restype = c.c_int64
     _LIB = lib
     return lib
 
@@ -259,6 +292,81 @@ class Problem:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.flr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request loop over the solver: `slots` concurrent solves, admission by device
+    memory footprint (flr_server_* in include/flr.h).  Inputs are borrowed until
+    wait() returns for the request; this object keeps references to them."""
+
+    def __init__(self, slots: int = 4, grid_per_slot: int = 0, hbm_budget: int = 0):
+        self._lib = load()
+        o = FlrServerOpts()
+        o.slots, o.grid_per_slot, o.hbm_budget = slots, grid_per_slot, hbm_budget
+        h = ctypes.c_void_p()
+        st = self._lib.flr_server_create(ctypes.byref(o), ctypes.byref(h))
+        if st != FLR_OK:
+            raise FlrError(st, "flr_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, X, y, graph, lam1, lam2, eps=1e-6, tol=1e-9, dtype=None, opts=None, **opt_kw):
+        torch = _torch()
+        if X.stride(1) != 1:
+            X = X.contiguous()
+        on_dev = X.is_cuda
+        y = y.to(device=X.device, dtype=torch.float64).contiguous()
+        keep = [X, y]
+        r = FlrRequest()
+        r.X, r.dtype, r.mem = X.data_ptr(), _dtype_code(X, dtype), FLR_MEM_DEVICE if on_dev else FLR_MEM_HOST
+        r.n, r.p, r.ldx = int(X.shape[0]), int(X.shape[1]), X.stride(0)
+        r.y = y.data_ptr()
+        r.E = _graph(graph, r.p, keep)
+        if r.E.kind == FLR_E_EDGES and on_dev and r.E.m:
+            keep[-1] = keep[-1].to(X.device)
+            r.E.edges = keep[-1].data_ptr()
+        r.lambda1, r.lambda2, r.eps, r.tol = float(lam1), float(lam2), float(eps), float(tol)
+        if opts is not None or opt_kw:
+            r.opts = opts if opts is not None else default_opts(**opt_kw)
+            r.use_opts = 1
+        rid = ctypes.c_uint64()
+        st = self._lib.flr_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid))
+        if st != FLR_OK:
+            raise FlrError(st, "flr_server_submit")
+        self._keep[rid.value] = (keep, r.p)
+        return rid.value
+
+    def poll(self, rid: int) -> bool:
+        d = ctypes.c_int32()
+        st = self._lib.flr_server_poll(self._h, rid, ctypes.byref(d))
+        if st != FLR_OK:
+            raise FlrError(st, "flr_server_poll")
+        return bool(d.value)
+
+    def wait(self, rid: int):
+        """(beta as numpy float64, FlrResult) for a submitted request."""
+        import numpy as np
+        _, p = self._keep[rid]
+        beta = np.zeros(p)
+        res = FlrResult()
+        self._lib.flr_server_wait(self._h, rid, beta.ctypes.data, ctypes.byref(res))
+        del self._keep[rid]
+        return beta, res
+
+    def footprint(self, n, p, m, dtype, host=True) -> int:
+        return int(self._lib.flr_footprint(n, p, m, DTYPE_CODES.get(dtype, dtype),
+                                           FLR_MEM_HOST if host else FLR_MEM_DEVICE))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.flr_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

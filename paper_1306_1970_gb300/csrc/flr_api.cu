@@ -100,7 +100,7 @@ struct flr_handle {
   void* ub0 = nullptr;
   void* ub1 = nullptr;
   unsigned char* ctl = nullptr;     // barrier counter, error flag, DevStats
-  unsigned char* hctl = nullptr;    // pinned copy of ctl
+  unsigned char hctl[256];          // host copy of ctl (read once per solve)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<void*> allocs;
   // batched tensor-core path (allocated on first use)
@@ -140,7 +140,8 @@ template <typename T>
 flr_status dalloc(flr_handle* h, T** out, size_t count) {
   void* ptr = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+  // stream-ordered: concurrent handles on other streams are not synchronised
+  cudaError_t e = cudaMallocAsync(&ptr, count * sizeof(T), h->stream);
   if (e != cudaSuccess) { (void)cudaGetLastError(); return FLR_ENOMEM; }
   h->allocs.push_back(ptr);
   *out = static_cast<T*>(ptr);
@@ -153,9 +154,9 @@ void release(flr_handle* h) {
   cudaGetDevice(&prev);
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
   h->allocs.clear();
-  if (h->hctl) cudaFreeHost(h->hctl);
+  if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   cudaSetDevice(prev);
@@ -202,8 +203,10 @@ flr_status build_csr(flr_handle* h, const int64_t* edges_host, long long m) {
   if ((s = dalloc(h, &h->rowptr, (size_t)p + 1)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->col, (size_t)std::max<long long>(1, 2 * m))) != FLR_OK) return s;
   if ((s = dalloc(h, &h->wc, (size_t)std::max<long long>(1, 2 * m))) != FLR_OK) return s;
-  FLR_TRY(cudaMemcpy(h->rowptr, rowptr.data(), sizeof(long long) * (p + 1), cudaMemcpyHostToDevice));
-  FLR_TRY(cudaMemcpy(h->col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice));
+  FLR_TRY(cudaMemcpyAsync(h->rowptr, rowptr.data(), sizeof(long long) * (p + 1), cudaMemcpyHostToDevice,
+                          h->stream));
+  FLR_TRY(cudaMemcpyAsync(h->col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice, h->stream));
+  FLR_TRY(cudaStreamSynchronize(h->stream));   // the host vectors go out of scope
   return FLR_OK;
 }
 
@@ -332,8 +335,12 @@ flr_status batch_group(flr_handle* h, int K, const double* l1, const double* l2,
   std::vector<double> hb((size_t)K * p);
   FLR_TRY(cudaMemcpyAsync(hb.data(), P.x, sizeof(double) * K * p, cudaMemcpyDeviceToHost, h->stream));
   FLR_TRY(cudaStreamSynchronize(h->stream));
-  FLR_TRY(cudaMemcpy(betas, hb.data(), sizeof(double) * K * p,
-                     io_mem == FLR_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice));
+  if (io_mem == FLR_MEM_HOST) {
+    std::memcpy(betas, hb.data(), sizeof(double) * K * p);
+  } else {
+    FLR_TRY(cudaMemcpyAsync(betas, hb.data(), sizeof(double) * K * p, cudaMemcpyHostToDevice, h->stream));
+    FLR_TRY(cudaStreamSynchronize(h->stream));
+  }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   int herr;
@@ -444,7 +451,9 @@ flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_
     std::vector<int64_t> eh((size_t)(2 * m));
     if (m > 0) {
       if (mem == FLR_MEM_HOST) std::memcpy(eh.data(), E->edges, sizeof(int64_t) * 2 * m);
-      else if (cudaMemcpy(eh.data(), E->edges, sizeof(int64_t) * 2 * m, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      else if (cudaMemcpyAsync(eh.data(), E->edges, sizeof(int64_t) * 2 * m, cudaMemcpyDeviceToHost,
+                               h->stream) != cudaSuccess ||
+               cudaStreamSynchronize(h->stream) != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(FLR_EINVAL);
       }
@@ -465,11 +474,10 @@ flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_
   if ((s = dalloc(h, &h->K2, P * kMaxLevels)) != FLR_OK) return fail(s);
   if (!h->wc && (s = dalloc(h, &h->wc, 1)) != FLR_OK) return fail(s);
   // u buffers hold doubles (the FP64 refinement pass) and floats (FP32 CG products)
-  if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->ub0), (size_t)h->ldn * 8)) != FLR_OK) return fail(s);
-  if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->ub1), (size_t)h->ldn * 8)) != FLR_OK) return fail(s);
+  if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->ub0), (size_t)h->ldn * 8 * kUR)) != FLR_OK) return fail(s);
+  if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->ub1), (size_t)h->ldn * 8 * kUR)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, &h->part, (size_t)2 * kNF * kMaxGrid)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, &h->ctl, 256)) != FLR_OK) return fail(s);
-  if (cudaMallocHost(&h->hctl, 256) != cudaSuccess) { (void)cudaGetLastError(); return fail(FLR_ENOMEM); }
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) return fail(FLR_ECUDA);
 
   // X -> column-major copy (padding rows are zero), y, then X^T y and diag(X^T X)
@@ -477,9 +485,12 @@ flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_
   const void* Xdev = X;
   void* staging = nullptr;
   if (mem == FLR_MEM_HOST) {
-    if (cudaMalloc(&staging, (size_t)(n * ldx) * es) != cudaSuccess) { (void)cudaGetLastError(); return fail(FLR_ENOMEM); }
+    if (cudaMallocAsync(&staging, (size_t)(n * ldx) * es, h->stream) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(FLR_ENOMEM);
+    }
     if (cudaMemcpyAsync(staging, X, (size_t)(n * ldx) * es, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
-      cudaFree(staging);
+      cudaFreeAsync(staging, h->stream);
       return fail(FLR_ECUDA);
     }
     Xdev = staging;
@@ -487,7 +498,7 @@ flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_
   if (cudaMemcpyAsync(h->y, y, sizeof(double) * n,
                       mem == FLR_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                       h->stream) != cudaSuccess) {
-    if (staging) cudaFree(staging);
+    if (staging) cudaFreeAsync(staging, h->stream);
     return fail(FLR_ECUDA);
   }
   switch (dtype) {
@@ -498,10 +509,12 @@ flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_
   }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (staging) cudaFree(staging);
+  if (staging) cudaFreeAsync(staging, h->stream);
   if (e != cudaSuccess) return fail(cuda_status(e));
   std::vector<double> ch((size_t)p);
-  if (cudaMemcpy(ch.data(), h->c, sizeof(double) * p, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(FLR_ECUDA);
+  if (cudaMemcpyAsync(ch.data(), h->c, sizeof(double) * p, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return fail(FLR_ECUDA);
   double s2 = 0.0;
   for (double v : ch) s2 += v * v;
   h->cnorm = std::sqrt(s2);
@@ -553,7 +566,7 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   DevStats* dst = reinterpret_cast<DevStats*>(h->ctl + 128);
   FLR_TRY(cudaMemsetAsync(h->ctl, 0, 128, h->stream));
   FLR_TRY(cudaMemsetAsync(h->ctl + 128, 0xff, 128, h->stream));   // status -1 until written
-  const size_t accsz = (size_t)h->ldn * 8;
+  const size_t accsz = (size_t)h->ldn * 8 * kUR;
   FLR_TRY(cudaMemsetAsync(h->ub0, 0, accsz, h->stream));
   FLR_TRY(cudaMemsetAsync(h->ub1, 0, accsz, h->stream));
   const double* binit = nullptr;

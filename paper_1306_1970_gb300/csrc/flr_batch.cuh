@@ -262,6 +262,13 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
   bool alive = gb.sync();
   int mm = 0, pcur = 0;
   auto is_own = [&](long long j) -> bool { return ((j / kTM) % G) == b; };
+  // In the tile loops below all 32 lanes of a warp share one RHS index k
+  // (128 columns per k, a multiple of 32), so per-RHS sums reduce by warp
+  // shuffles and one shared-memory atomic per warp.
+  auto wadd = [&](double* dst, double v) {
+    v = warp_sum(v);
+    if ((tid & 31) == 0 && v != 0.0) atomicAdd(dst, v);
+  };
 
   while (alive) {
     // ---------------- reweight (Eq. lin-sys) per active RHS; S x; penalties
@@ -270,9 +277,10 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
     for (long long t = b; t < ntiles; t += G) {
       for (int e = tid; e < K * kTM; e += kBT) {
         const int k = e / kTM;
-        if (!s_act[k]) continue;
+        if (!s_act[k]) continue;                    // warp-uniform
         const long long j = t * kTM + (e % kTM);
-        if (j >= p) continue;
+        double v_pen1 = 0.0, v_pen2 = 0.0;
+        if (j < p) {
         const double* xk = P.x + (long long)k * p;
         const double xj = ldcg(xk + j);
         const double l1 = P.lam1[k], l2 = P.lam2[k];
@@ -289,8 +297,11 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         const double deg = (wl_ + wr_) + (wu_ + wd_);
         P.idg[o] = 1.0 / fma(l2, deg, la + P.d[j]);
         P.q[o] = fma(la, xj, l2 * lap);
-        atomicAdd(&s_pen[k], fabs(xj));
-        if (pen2 != 0.0) atomicAdd(&s_pen[kNRMax + k], pen2);
+        v_pen1 = fabs(xj);
+        v_pen2 = pen2;
+        }
+        wadd(&s_pen[k], v_pen1);
+        wadd(&s_pen[kNRMax + k], v_pen2);
       }
     }
     // ---------------- FP64 refinement pass 1: U0 = X b (CUDA cores, FP64)
@@ -409,13 +420,18 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         for (int e = tid; e < K * kTM; e += kBT) {
           const int k = e / kTM;
           const long long j = t * kTM + (e % kTM);
-          if (j >= p || !s_act[k]) continue;
-          const long long o = (long long)k * p + j;
-          const double rj = (P.c[j] - P.t0[o]) - P.q[o];
-          const double zj = rj * P.idg[o];
-          P.r[o] = rj; P.z[o] = zj; pc[o] = zj;
-          atomicAdd(&s_rz[k], rj * zj);
-          atomicAdd(&s_rr[k], rj * rj);
+          if (!s_act[k]) continue;                  // warp-uniform
+          double v_rz = 0.0, v_rr = 0.0;
+          if (j < p) {
+            const long long o = (long long)k * p + j;
+            const double rj = (P.c[j] - P.t0[o]) - P.q[o];
+            const double zj = rj * P.idg[o];
+            P.r[o] = rj; P.z[o] = zj; pc[o] = zj;
+            v_rz = rj * zj;
+            v_rr = rj * rj;
+          }
+          wadd(&s_rz[k], v_rz);
+          wadd(&s_rr[k], v_rr);
         }
       }
     }
@@ -455,10 +471,10 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         for (int e = tid; e < NR * kTM; e += kBT) {
           const int k = e / kTM;
           const long long j = t * kTM + (e % kTM);
-          if (j >= p) continue;
           const long long o = (long long)k * p + j;
           __nv_bfloat16 h = __float2bfloat16(0.f), m = h, l = h;
-          if (k < K && s_cga[k]) {
+          double v_psp = 0.0;
+          if (j < p && k < K && s_cga[k]) {
             const double g = s_gam[k];
             auto pv = [&](long long kk) -> double {
               const long long ok = (long long)k * p + kk;
@@ -475,12 +491,15 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
             if (j + q2 < p) lap = fma(P.wd[o], pj - pv(j + q2), lap);
             const double spj = fma(P.la[o], pj, lap);
             P.q[o] = spj;
-            atomicAdd(&s_psp[k], pj * spj);
+            v_psp = pj * spj;
             split3(pj, h, m, l);
           }
-          P.Ps[(0LL * NR + k) * P.ldp + j] = h;
-          P.Ps[(1LL * NR + k) * P.ldp + j] = m;
-          P.Ps[(2LL * NR + k) * P.ldp + j] = l;
+          if (k < K) wadd(&s_psp[k], v_psp);       // k is warp-uniform
+          if (j < p) {
+            P.Ps[(0LL * NR + k) * P.ldp + j] = h;
+            P.Ps[(1LL * NR + k) * P.ldp + j] = m;
+            P.Ps[(2LL * NR + k) * P.ldp + j] = l;
+          }
         }
       }
       __syncthreads();
@@ -554,17 +573,22 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         for (int e = tid; e < K * kTM; e += kBT) {
           const int k = e / kTM, cl = e % kTM;
           const long long j = t * kTM + cl;
-          if (j >= p || !s_cga[k]) continue;
-          const long long o = (long long)k * p + j;
-          const double nu = s_nu[k];
-          const double qj = (double)ts[k * kTM + cl] + P.q[o];
-          P.x[o] = fma(nu, pc[o], P.x[o]);
-          const double rj = fma(-nu, qj, P.r[o]);
-          const double zj = rj * P.idg[o];
-          P.r[o] = rj;
-          P.z[o] = zj;
-          atomicAdd(&loc[k], rj * zj);
-          atomicAdd(&loc[kNRMax + k], rj * rj);
+          if (!s_cga[k]) continue;                  // warp-uniform
+          double v_rz = 0.0, v_rr = 0.0;
+          if (j < p) {
+            const long long o = (long long)k * p + j;
+            const double nu = s_nu[k];
+            const double qj = (double)ts[k * kTM + cl] + P.q[o];
+            P.x[o] = fma(nu, pc[o], P.x[o]);
+            const double rj = fma(-nu, qj, P.r[o]);
+            const double zj = rj * P.idg[o];
+            P.r[o] = rj;
+            P.z[o] = zj;
+            v_rz = rj * zj;
+            v_rr = rj * rj;
+          }
+          wadd(&loc[k], v_rz);
+          wadd(&loc[kNRMax + k], v_rr);
         }
         __syncthreads();
       }

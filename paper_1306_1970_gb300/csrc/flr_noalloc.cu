@@ -201,7 +201,7 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   const size_t o_vec = off;  off += 9 * vecb;                       // x r z pb0 pb1 q c d binv
   const size_t o_k = off;
   if (precond != FLR_PC_JACOBI) off += 2 * up256(sizeof(double) * (size_t)levels * (size_t)p);
-  const size_t o_u = off;    off += 2 * up256(sizeof(double) * (size_t)ldn);
+  const size_t o_u = off;    off += 2 * up256(sizeof(double) * (size_t)ldn * kUR);
   if (off > (size_t)FLR_NOALLOC_SCRATCH_BYTES) return FLR_ESCRATCH;
   if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
 
@@ -212,13 +212,13 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   double* vec[9];
   for (int i = 0; i < 9; ++i) vec[i] = reinterpret_cast<double*>(S + o_vec + i * vecb);
   double* ub0 = reinterpret_cast<double*>(S + o_u);
-  double* ub1 = reinterpret_cast<double*>(S + o_u + up256(sizeof(double) * (size_t)ldn));
+  double* ub1 = reinterpret_cast<double*>(S + o_u + up256(sizeof(double) * (size_t)ldn * kUR));
 
   // ---- what must start at zero (the array keeps the previous call's contents)
   if (cudaMemsetAsync(S + o_ctl, 0, 128, st) != cudaSuccess ||
       cudaMemsetAsync(S + o_ctl + 128, 0xff, 128, st) != cudaSuccess ||
-      cudaMemsetAsync(ub0, 0, sizeof(double) * ldn, st) != cudaSuccess ||
-      cudaMemsetAsync(ub1, 0, sizeof(double) * ldn, st) != cudaSuccess) {
+      cudaMemsetAsync(ub0, 0, sizeof(double) * ldn * kUR, st) != cudaSuccess ||
+      cudaMemsetAsync(ub1, 0, sizeof(double) * ldn * kUR, st) != cudaSuccess) {
     (void)cudaGetLastError();
     return FLR_ECUDA;
   }

@@ -1,0 +1,220 @@
+// Serving loop over the FLR solver: slots, admission by device-memory
+// footprint, concurrent solves on separate streams (see include/flr.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/flr.h"
+
+namespace {
+
+struct Job {
+  uint64_t id;
+  flr_request r;
+  int64_t footprint;
+  double t_submit;
+};
+
+struct Done {
+  flr_result res;
+  std::vector<double> beta;
+};
+
+}  // namespace
+
+struct flr_server {
+  flr_server_opts o{};
+  int device = 0;
+  int sm_count = 0;
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> streams;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Job> queue;
+  std::unordered_map<uint64_t, Done> done;
+  std::unordered_map<uint64_t, bool> pending;   // submitted, not yet finished
+  int64_t in_use = 0;
+  uint64_t next_id = 1;
+  bool stopping = false;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  void worker(int slot);
+};
+
+namespace {
+
+size_t esz(int dt) { return dt == FLR_F64 ? 8 : dt == FLR_F32 ? 4 : (dt == FLR_BF16 || dt == FLR_F16) ? 2 : 0; }
+
+long long graph_edges(const flr_graph& E, long long p) {
+  if (E.kind == FLR_E_CHAIN) return p - 1;
+  if (E.kind == FLR_E_LATTICE) return E.q1 * (E.q2 - 1) + (E.q1 - 1) * E.q2;
+  return E.m;
+}
+
+}  // namespace
+
+extern "C" int64_t flr_footprint(int64_t n, int64_t p, int64_t m, int32_t dtype, int32_t mem) {
+  const size_t es = esz(dtype);
+  if (es == 0 || n < 1 || p < 1) return -1;
+  const int64_t vec = 16 / (int64_t)es;
+  const int64_t ldn = (n + vec - 1) / vec * vec;
+  int64_t b = p * ldn * (int64_t)es;                 // column-major copy of X
+  if (mem == FLR_MEM_HOST) b += n * p * (int64_t)es; // staging during flr_create
+  b += 8 * n + 16 * ldn;                             // y, u buffers
+  b += 8 * p * (15 + 2 * 13);                        // FP64 vectors and PCR multipliers
+  b += (8 + 4 + 8) * 2 * std::max<int64_t>(m, 1) + 8 * (p + 1);   // CSR
+  b += 64 * 1024;                                    // partials, control
+  return b;
+}
+
+void flr_server::worker(int slot) {
+  cudaSetDevice(device);
+  while (true) {
+    Job job;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      auto pick = [&]() -> bool {
+        for (auto it = queue.begin(); it != queue.end(); ++it)
+          if (in_use + it->footprint <= o.hbm_budget) return true;
+        return false;
+      };
+      cv_work.wait(lk, [&] { return pick() || (stopping && queue.empty()); });
+      if (queue.empty()) return;   // stopping
+      auto it = queue.begin();
+      while (in_use + it->footprint > o.hbm_budget) ++it;
+      job = *it;
+      queue.erase(it);
+      in_use += job.footprint;
+    }
+    Done d;
+    d.res = flr_result{};
+    d.res.slot = slot;
+    d.res.t_submit = job.t_submit;
+    d.res.t_start = now();
+    d.res.footprint = job.footprint;
+    d.beta.assign((size_t)job.r.p, 0.0);
+    const flr_request& r = job.r;
+    flr_t h = nullptr;
+    flr_status st = flr_create(r.X, r.dtype, r.n, r.p, r.ldx, r.y, &r.E, r.mem, streams[slot], &h);
+    if (st == FLR_OK) {
+      flr_opts op;
+      flr_default_opts(&op);
+      if (r.use_opts) op = r.opts;
+      // the solve kernel's own sizing rule, capped at the slot's share of the SMs
+      const long long per_block = r.dtype == FLR_F64 ? 8192 : 65536;
+      long long g = op.grid > 0 ? op.grid : (r.n * r.p + per_block - 1) / per_block;
+      op.grid = (int32_t)std::max<long long>(1, std::min<long long>(g, o.grid_per_slot));
+      st = flr_solve(h, r.lambda1, r.lambda2, r.eps, r.tol, &op, nullptr, d.beta.data(), FLR_MEM_HOST,
+                     &d.res.stats);
+      flr_destroy(h);
+    }
+    d.res.status = st;
+    d.res.t_end = now();
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      in_use -= job.footprint;
+      done[job.id] = std::move(d);
+      pending.erase(job.id);
+    }
+    cv_done.notify_all();
+    cv_work.notify_all();
+  }
+}
+
+extern "C" flr_status flr_server_create(const flr_server_opts* opts, flr_server_t* out) {
+  if (!out) return FLR_EINVAL;
+  *out = nullptr;
+  flr_server* s = new (std::nothrow) flr_server();
+  if (!s) return FLR_ENOMEM;
+  if (cudaGetDevice(&s->device) != cudaSuccess) { (void)cudaGetLastError(); delete s; return FLR_ECUDA; }
+  cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+  if (opts) s->o = *opts;
+  if (s->o.slots <= 0) s->o.slots = 4;
+  if (s->o.grid_per_slot <= 0) s->o.grid_per_slot = std::max(1, s->sm_count / s->o.slots);
+  if (s->o.hbm_budget <= 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { (void)cudaGetLastError(); delete s; return FLR_ECUDA; }
+    s->o.hbm_budget = (int64_t)(fr / 4 * 3);
+  }
+  if ((long long)s->o.slots * s->o.grid_per_slot > s->sm_count) {
+    delete s;   // cooperative solves must all fit on the device at once
+    return FLR_EINVAL;
+  }
+  for (int i = 0; i < s->o.slots; ++i) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      (void)cudaGetLastError();
+      for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+      delete s;
+      return FLR_ECUDA;
+    }
+    s->streams.push_back(st);
+  }
+  for (int i = 0; i < s->o.slots; ++i) s->workers.emplace_back(&flr_server::worker, s, i);
+  *out = s;
+  return FLR_OK;
+}
+
+extern "C" flr_status flr_server_submit(flr_server_t s, const flr_request* r, uint64_t* id) {
+  if (!s || !r || !id) return FLR_EINVAL;
+  if (!r->X || !r->y || r->n < 1 || r->p < 1 || r->ldx < r->p || esz(r->dtype) == 0) return FLR_EINVAL;
+  if (r->mem != FLR_MEM_HOST && r->mem != FLR_MEM_DEVICE) return FLR_EINVAL;
+  if (!(r->lambda1 >= 0.0) || !(r->lambda2 >= 0.0) || !(r->eps > 0.0) || !(r->tol > 0.0)) return FLR_EINVAL;
+  if (r->E.kind != FLR_E_CHAIN && r->E.kind != FLR_E_LATTICE && r->E.kind != FLR_E_EDGES) return FLR_EINVAL;
+  const int64_t fp = flr_footprint(r->n, r->p, graph_edges(r->E, r->p), r->dtype, r->mem);
+  if (fp < 0) return FLR_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stopping) return FLR_EINVAL;
+  if (fp > s->o.hbm_budget) return FLR_ENOMEM;
+  Job j{s->next_id++, *r, fp, s->now()};
+  s->pending[j.id] = true;
+  s->queue.push_back(j);
+  *id = j.id;
+  s->cv_work.notify_one();
+  return FLR_OK;
+}
+
+extern "C" flr_status flr_server_poll(flr_server_t s, uint64_t id, int32_t* is_done) {
+  if (!s || !is_done) return FLR_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->done.count(id)) { *is_done = 1; return FLR_OK; }
+  if (s->pending.count(id)) { *is_done = 0; return FLR_OK; }
+  return FLR_EINVAL;
+}
+
+extern "C" flr_status flr_server_wait(flr_server_t s, uint64_t id, double* beta_out, flr_result* res) {
+  if (!s) return FLR_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (!s->done.count(id) && !s->pending.count(id)) return FLR_EINVAL;
+  s->cv_done.wait(lk, [&] { return s->done.count(id) > 0; });
+  Done d = std::move(s->done[id]);
+  s->done.erase(id);
+  lk.unlock();
+  if (beta_out) std::memcpy(beta_out, d.beta.data(), sizeof(double) * d.beta.size());
+  if (res) *res = d.res;
+  return (flr_status)d.res.status;
+}
+
+extern "C" flr_status flr_server_destroy(flr_server_t s) {
+  if (!s) return FLR_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stopping = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->workers) t.join();
+  for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+  delete s;
+  return FLR_OK;
+}

@@ -53,6 +53,8 @@ enum SolveStatus : int {
 enum NbrBits : unsigned char { NB_L = 1, NB_R = 2, NB_U = 4, NB_D = 8 };
 
 constexpr int kRF = 2;   // fields per block reduction
+constexpr int kUR = 1;   // replicas of each u accumulator: block b adds into replica b % kUR,
+                         // spreading the atomics of X p over kUR times more L2 lines
 
 struct SolveParams {
   const void* Xt;
@@ -71,8 +73,8 @@ struct SolveParams {
   const double* beta_init;   // nullptr -> X_j^T y / X_j^T X_j
   // state
   double *x, *r, *z, *pb0, *pb1, *q, *a, *wL, *wR, *wU, *wD, *wc, *idg, *K1, *K2, *binv;
-  void* ub0;                 // two n-vectors of doubles (also used as floats)
-  void* ub1;
+  void* ub0;                 // two accumulators, each kUR replicas of ldn doubles
+  void* ub1;                 // (replica r at byte offset 8 * r * ldn; also used as floats)
   double* part;              // [2 slots][kNF][gridDim.x]
   unsigned* bar;
   int* err;
@@ -343,27 +345,30 @@ __device__ __forceinline__ void apply_precond(const SolveParams& P, long long j0
   __syncthreads();
 }
 
-// Copy an n-vector (ldn entries, padding zero) from global to shared memory with
-// 16-byte coherent loads; returns this thread's partial sum of squares of the
-// first n entries (FP64), and optionally of (y - u)^2.
+// Sum the kUR replicas of an n-vector accumulator (ldn entries each, padding
+// zero; replica r at byte offset 8 * r * ldn) into shared memory with 16-byte
+// coherent loads, in a fixed replica order; returns this thread's partial sum
+// of squares of the first n entries (FP64), or of (y - u)^2 when `resid`.
 template <typename A>
 __device__ __forceinline__ double stage_u(const A* __restrict__ u, A* us, long long n, long long ldn,
                                           const double* y, bool resid) {
   constexpr int VA = 16 / sizeof(A);
   const int nvec = (int)(ldn / VA);
+  const long long rstride = ldn * 8 / (long long)sizeof(A);   // elements between replicas
   double acc = 0.0;
   for (int v = threadIdx.x; v < nvec; v += kThreads) {
     A t[VA];
-    if constexpr (VA == 4) {
-      const float4 q = __ldcg(reinterpret_cast<const float4*>(u) + v);
-      const float tt[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-      for (int e = 0; e < VA; ++e) t[e] = (A)tt[e % 4];
-    } else {
-      const double2 q = __ldcg(reinterpret_cast<const double2*>(u) + v);
-      const double tt[2] = {q.x, q.y};
+    for (int e = 0; e < VA; ++e) t[e] = A(0);
 #pragma unroll
-      for (int e = 0; e < VA; ++e) t[e] = (A)tt[e % 2];
+    for (int r = 0; r < kUR; ++r) {
+      if constexpr (VA == 4) {
+        const float4 q = __ldcg(reinterpret_cast<const float4*>(u + r * rstride) + v);
+        t[0] += (A)q.x; t[1] += (A)q.y; t[2] += (A)q.z; t[3] += (A)q.w;
+      } else {
+        const double2 q = __ldcg(reinterpret_cast<const double2*>(u + r * rstride) + v);
+        t[0] += (A)q.x; t[1] += (A)q.y;
+      }
     }
 #pragma unroll
     for (int e = 0; e < VA; ++e) {
@@ -446,10 +451,12 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
     slot ^= 1;
     return true;
   };
-  auto zero_u = [&](void* buf) {   // this block's chunk of an n-vector of doubles
+  auto zero_u = [&](void* buf) {   // this block's chunk of every replica
     double* u = reinterpret_cast<double*>(buf);
-    for (long long i = zs0 + tid; i < ze0; i += kThreads) u[i] = 0.0;
+    for (int r = 0; r < kUR; ++r)
+      for (long long i = zs0 + tid; i < ze0; i += kThreads) u[(long long)r * P.ldn + i] = 0.0;
   };
+  const int rep = b % kUR;   // this block's accumulator replica
 
   // ---- initialisation (Algorithm 1): beta_j = X_j^T y / X_j^T X_j
   for (int jj = tid; jj < wl; jj += kThreads) {
@@ -523,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
     if (P.precond != PC_JACOBI && GK == GK_STENCIL) setup_tridiag(P, j0, wl, tv, s_wl, s_wr, pw);
     // ---------------- u0 = X x in FP64 (refinement pass)
     zero_u(U1);
-    phase_a<TX, double>(P, Xt, j0, wl, vsd, redd, reinterpret_cast<double*>(U0));
+    phase_a<TX, double>(P, Xt, j0, wl, vsd, redd, reinterpret_cast<double*>(U0) + (long long)rep * P.ldn);
     block_reduce<2>(pen, rs, ncol);
     if (!grid_sum(pen)) return;
     // ---------------- f(beta(r)) (Eq. obj) and the outer stop test
@@ -607,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       }
       zero_u(Unext);
       __syncthreads();
-      phase_a<TX, Acc>(P, Xt, j0, wl, vs, red, Ucur);
+      phase_a<TX, Acc>(P, Xt, j0, wl, vs, red, Ucur + (long long)rep * P.ldn * 8 / (long long)sizeof(Acc));
       block_reduce<1>(sv, rs, ncol);
       if (!grid_sum(sv)) return;
       // p^T Q p = ||X p||^2 + p^T S p

@@ -63,3 +63,17 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert lib.flr_create(buf, 9, 10, 5, 5, buf, ctypes.byref(g), 1, None, ctypes.byref(out)) == 1
     g.kind, g.q1, g.q2 = flr.FLR_E_LATTICE, 2, 3
     assert lib.flr_create(buf, 1, 10, 5, 5, buf, ctypes.byref(g), 1, None, ctypes.byref(out)) == 1
+
+
+def test_footprint_estimate_is_monotone_and_validates(lib):
+    lib.flr_footprint.restype = ctypes.c_int64
+    lib.flr_footprint.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                  ctypes.c_int32]
+    f = lib.flr_footprint
+    base = f(1000, 10000, 19800, 1, 0)
+    assert base >= 1000 * 10000 * 4          # at least the column-major copy of X
+    assert f(1000, 10000, 19800, 1, 1) > base  # host inputs add a staging copy
+    assert f(2000, 10000, 19800, 1, 0) > base
+    assert f(1000, 20000, 19800, 1, 0) > base
+    assert f(1000, 10000, 19800, 2, 0) < base  # 16-bit X
+    assert f(0, 10, 9, 1, 0) < 0 and f(10, 10, 9, 7, 0) < 0
