@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--impl", default="flr", choices=["flr", "reference"])
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--tol-cg", type=float, default=1e-8)
-    ap.add_argument("--precond", default="jacobi")
+    ap.add_argument("--precond", default="auto")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=120, help="served stream length (serve5)")
@@ -48,6 +48,7 @@ def parse():
                     help="one solve of a workload (for profiler captures), then exit")
     ap.add_argument("--max-mm", type=int, default=20000)
     ap.add_argument("--max-cg", type=int, default=10000)
+    ap.add_argument("--grid", type=int, default=0, help="solve-kernel blocks (0 = automatic)")
     return ap.parse_args()
 
 
@@ -92,12 +93,12 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the sources the single-problem solve kernel is built from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1306_1970_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, fn), "rb") as fh:
-                h.update(fh.read())
+    for fn in ("flr_device.cuh", "flr_solve.cuh"):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -330,10 +331,11 @@ def solve_once(args):
     y = torch.from_numpy(pr.y).cuda()
     prob = flr.Problem(X, y, pr.graph)
     _, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=args.tol, precond=args.precond,
-                       tol_cg=args.tol_cg, max_mm=args.max_mm, max_cg=args.max_cg)
+                       tol_cg=args.tol_cg, max_mm=args.max_mm, max_cg=args.max_cg, grid=args.grid)
     torch.cuda.synchronize()
     print(json.dumps({"once": args.once, "n": pr.n, "p": pr.p, "mm_iters": st.mm_iters,
-                      "cg_iters": st.cg_iters, "status": st.status, "ms": st.ms, "f": st.f}))
+                      "cg_iters": st.cg_iters, "status": st.status, "ms": st.ms, "f": st.f,
+                      "grid": st.grid, "us_per_cg": 1000.0 * st.ms / max(1, st.cg_iters)}))
 
 
 def main():

@@ -23,7 +23,7 @@ FLR_EBREAKDOWN, FLR_ENONFINITE, FLR_ETIMEOUT, FLR_ENOTIMPL, FLR_ESCRATCH = 5, 6,
 FLR_F64, FLR_F32, FLR_BF16, FLR_F16 = 0, 1, 2, 3
 FLR_MEM_DEVICE, FLR_MEM_HOST = 0, 1
 FLR_E_CHAIN, FLR_E_LATTICE, FLR_E_EDGES = 0, 1, 2
-PRECOND = {"auto": 0, "jacobi": 1, "tridiag": 2, "paper": 3}
+PRECOND = {"auto": 0, "jacobi": 1, "tridiag": 2, "paper": 3, "twolevel": 4}
 DTYPE_CODES = {"f64": FLR_F64, "f32": FLR_F32, "bf16": FLR_BF16, "f16": FLR_F16}
 
 # every symbol declared in include/flr.h
@@ -42,7 +42,7 @@ class FlrOpts(ctypes.Structure):
     _fields_ = [("max_mm", ctypes.c_int32), ("max_cg", ctypes.c_int32), ("min_cg", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("tol_cg", ctypes.c_double), ("grid", ctypes.c_int32),
                 ("inject_stall", ctypes.c_int32), ("wait_cycles", ctypes.c_int64),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("refine_every", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class FlrStats(ctypes.Structure):

@@ -94,9 +94,11 @@ struct flr_handle {
   long long* rowptr = nullptr;
   int* col = nullptr;
   // solve workspace
-  double *x = nullptr, *r = nullptr, *z = nullptr, *pb0 = nullptr, *pb1 = nullptr, *q = nullptr,
-         *a = nullptr, *wL = nullptr, *wR = nullptr, *wU = nullptr, *wD = nullptr, *wc = nullptr,
-         *idg = nullptr, *K1 = nullptr, *K2 = nullptr, *binv = nullptr, *part = nullptr;
+  double *x = nullptr, *z = nullptr, *pb0 = nullptr, *pb1 = nullptr, *wc = nullptr, *K1 = nullptr,
+         *K2 = nullptr, *binv = nullptr, *part = nullptr;
+  // two-level preconditioner
+  int *uf = nullptr, *cmap = nullptr, *cid = nullptr;
+  double *qcinv = nullptr, *qc = nullptr, *qci = nullptr, *sc0 = nullptr, *sc1 = nullptr;
   void* ub0 = nullptr;
   void* ub1 = nullptr;
   unsigned char* ctl = nullptr;     // barrier counter, error flag, DevStats
@@ -109,9 +111,10 @@ struct flr_handle {
   int bS = 1;
   long long bkchunk = 0;
   __nv_bfloat16* Xr = nullptr;
-  double* bvec[13] = {nullptr};
+  double* bvec[15] = {nullptr};
   __nv_bfloat16 *Ps = nullptr, *Us = nullptr;
   float* Upart = nullptr;
+  float* Uf = nullptr;
   double *U0part = nullptr, *U0 = nullptr, *bred = nullptr, *blam = nullptr;
   unsigned char* bctl = nullptr;
   BatchStats* bstats = nullptr;
@@ -213,7 +216,13 @@ flr_status build_csr(flr_handle* h, const int64_t* edges_host, long long m) {
 template <typename TX, int GK>
 flr_status launch_solve_t(flr_handle* h, SolveParams& P, int G, size_t smem) {
   auto kern = mm_solve_kernel<TX, GK>;
-  FLR_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // The attribute is per kernel, shared by every thread of the process: set it
+  // to the device maximum (the same value from every caller), never to this
+  // launch's size, which a concurrent solve could lower before this launch.
+  int smem_max = 0;
+  FLR_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+  if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
+  FLR_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   int nb = 0;
   FLR_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem));
   if (nb < 1 || G > nb * h->sm_count) return FLR_ENOTIMPL;
@@ -252,12 +261,13 @@ flr_status batch_prepare(flr_handle* h) {
   h->bS = S;
   h->bkchunk = kchunk;
   if ((s = dalloc(h, &h->Xr, (size_t)(n * h->ldp))) != FLR_OK) return s;
-  for (int i = 0; i < 13; ++i)
+  for (int i = 0; i < 15; ++i)
     if ((s = dalloc(h, &h->bvec[i], (size_t)kNRMax * p)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->Ps, (size_t)kSlices * kNRMax * h->ldp)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->Us, (size_t)kSlices * kNRMax * h->ldn)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->Upart, (size_t)S * kNRMax * n)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->U0part, (size_t)S * kNRMax * n)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->Uf, (size_t)kNRMax * n)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->U0, (size_t)kNRMax * n)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->bred, (size_t)kRedSlots * 4 * kNRMax)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->blam, (size_t)2 * kNRMax)) != FLR_OK) return s;
@@ -305,7 +315,15 @@ flr_status batch_group(flr_handle* h, int K, const double* l1, const double* l2,
   double** v = h->bvec;
   P.x = v[0]; P.r = v[1]; P.z = v[2]; P.pb0 = v[3]; P.pb1 = v[4]; P.q = v[5]; P.la = v[6];
   P.wl = v[7]; P.wr = v[8]; P.wu = v[9]; P.wd = v[10]; P.idg = v[11]; P.t0 = v[12];
+  P.lmul = v[13]; P.dinv = v[14];
+  {
+    int pc = o.precond;
+    if (pc == FLR_PC_AUTO) pc = FLR_PC_TRIDIAG;
+    P.precond = pc == FLR_PC_TRIDIAG ? PC_TRIDIAG : pc == FLR_PC_PAPER ? PC_PAPER : PC_JACOBI;
+  }
   P.Ps = h->Ps; P.Us = h->Us; P.Upart = h->Upart; P.U0part = h->U0part; P.U0 = h->U0;
+  P.Uf = h->Uf;
+  P.refine_every = o.refine_every > 0 ? o.refine_every : 8;
   P.red = h->bred;
   P.bar = reinterpret_cast<unsigned*>(h->bctl);
   P.err = reinterpret_cast<int*>(h->bctl + 64);
@@ -315,7 +333,7 @@ flr_status batch_group(flr_handle* h, int K, const double* l1, const double* l2,
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
-  FLR_TRY(cudaFuncSetAttribute(mm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FLR_TRY(cudaFuncSetAttribute(mm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   int nb = 0;
   FLR_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mm_batch_kernel, kBT, smem));
   if (nb < 1) return FLR_ENOTIMPL;
@@ -466,9 +484,12 @@ flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_
   if ((s = dalloc(h, &h->y, (size_t)n)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, &h->c, P)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, &h->d, P)) != FLR_OK) return fail(s);
-  double** vecs[] = {&h->x, &h->r, &h->z, &h->pb0, &h->pb1, &h->q, &h->a, &h->wL, &h->wR,
-                     &h->wU, &h->wD, &h->idg, &h->binv};
+  double** vecs[] = {&h->x, &h->z, &h->pb0, &h->pb1, &h->binv,
+                     &h->qcinv, &h->qc, &h->qci, &h->sc0, &h->sc1};
   for (double** v : vecs)
+    if ((s = dalloc(h, v, P)) != FLR_OK) return fail(s);
+  int** ivecs[] = {&h->uf, &h->cmap, &h->cid};
+  for (int** v : ivecs)
     if ((s = dalloc(h, v, P)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, &h->K1, P * kMaxLevels)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, &h->K2, P * kMaxLevels)) != FLR_OK) return fail(s);
@@ -533,16 +554,19 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   flr_opts o;
   flr_default_opts(&o);
   if (opts) o = *opts;
-  if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0)
+  if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0 ||
+      o.refine_every < 0)
     return FLR_EINVAL;
   int prev_dev = 0;
   cudaGetDevice(&prev_dev);
   if (prev_dev != h->device) cudaSetDevice(h->device);
 
   int precond = o.precond;
-  if (precond == FLR_PC_AUTO) precond = h->gkind == FLR_E_CHAIN ? FLR_PC_TRIDIAG : FLR_PC_JACOBI;
-  if (precond != FLR_PC_JACOBI && precond != FLR_PC_TRIDIAG && precond != FLR_PC_PAPER) return FLR_EINVAL;
-  if (precond != FLR_PC_JACOBI && h->gkind == FLR_E_EDGES) return FLR_ENOTIMPL;
+  if (precond == FLR_PC_AUTO) precond = h->gkind == FLR_E_CHAIN ? FLR_PC_TRIDIAG : FLR_PC_TWOLEVEL;
+  if (precond != FLR_PC_JACOBI && precond != FLR_PC_TRIDIAG && precond != FLR_PC_PAPER &&
+      precond != FLR_PC_TWOLEVEL)
+    return FLR_EINVAL;
+  if ((precond == FLR_PC_TRIDIAG || precond == FLR_PC_PAPER) && h->gkind == FLR_E_EDGES) return FLR_ENOTIMPL;
 
   // grid: one block per SM at most; fewer for small problems
   const long long work = h->n * h->p;
@@ -587,9 +611,10 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   P.max_mm = o.max_mm; P.max_cg = o.max_cg; P.min_cg = o.min_cg; P.precond = precond;
   P.w = w; P.wpad = wpad; P.levels = levels;
   P.beta_init = binit;
-  P.x = h->x; P.r = h->r; P.z = h->z; P.pb0 = h->pb0; P.pb1 = h->pb1; P.q = h->q; P.a = h->a;
-  P.wL = h->wL; P.wR = h->wR; P.wU = h->wU; P.wD = h->wD; P.wc = h->wc; P.idg = h->idg;
+  P.x = h->x; P.z = h->z; P.pb0 = h->pb0; P.pb1 = h->pb1; P.wc = h->wc;
   P.K1 = h->K1; P.K2 = h->K2; P.binv = h->binv;
+  P.uf = h->uf; P.cmap = h->cmap; P.cid = h->cid; P.ncomp = reinterpret_cast<int*>(h->ctl + 96);
+  P.qcinv = h->qcinv; P.qc = h->qc; P.qci = h->qci; P.sc0 = h->sc0; P.sc1 = h->sc1;
   P.ub0 = h->ub0; P.ub1 = h->ub1; P.part = h->part;
   P.bar = bar; P.err = err; P.stats = dst;
   P.timeout = o.wait_cycles > 0 ? o.wait_cycles : (1LL << 33);   // ~4 s of SM clock
@@ -639,8 +664,9 @@ flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const doub
   flr_default_opts(&o);
   if (opts) o = *opts;
   // tensor-core multi-RHS path: BF16 X, chain/lattice, Jacobi preconditioner
-  const bool tc_path = h->dtype == FLR_BF16 && h->gkind != FLR_E_EDGES &&
-                       (o.precond == FLR_PC_AUTO || o.precond == FLR_PC_JACOBI) && K >= 1;
+  const bool tc_path = h->dtype == FLR_BF16 && h->gkind != FLR_E_EDGES && K >= 1 &&
+                       (o.precond == FLR_PC_AUTO || o.precond == FLR_PC_JACOBI ||
+                        o.precond == FLR_PC_TRIDIAG || o.precond == FLR_PC_PAPER);
   if (tc_path) {
     flr_status first = FLR_OK;
     for (int k0 = 0; k0 < K; k0 += kNRMax) {

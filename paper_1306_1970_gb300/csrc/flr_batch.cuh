@@ -50,13 +50,17 @@ struct BatchParams {
   const double* lam2;
   double eps, tol, tol_cg;
   int max_mm, max_cg, min_cg;
+  int precond;                 // PC_JACOBI, PC_TRIDIAG or PC_PAPER
+  int refine_every;            // exact FP64 X b / X^T X b every this many MM iterations
   int S;                       // split-K chunks per row tile in phase A
   long long kchunk;            // columns per split-K chunk (multiple of 64)
   // per-RHS FP64 state, layout [k][j]
   double *x, *r, *z, *pb0, *pb1, *q, *la, *wl, *wr, *wu, *wd, *idg, *t0;
+  double *lmul, *dinv;         // tile tridiagonal LU: multipliers and 1/pivots
   __nv_bfloat16* Ps;           // [3][NR][ldp]
   __nv_bfloat16* Us;           // [3][NR][ldn]
   float* Upart;                // [S][NR][n]
+  float* Uf;                   // [NR][n]  U = X p of the current CG iteration
   double* U0part;              // [S][NR][n]
   double* U0;                  // [NR][n]
   double* red;                 // [kRedSlots][4*kNRMax]
@@ -192,6 +196,53 @@ __device__ __forceinline__ void tmem_to_smem(uint32_t tmem, float* ts, int NR) {
   __syncthreads();
 }
 
+// Thomas factorisation of the tridiagonal preconditioner of RHS k on the
+// 128-column tile starting at j0 (couplings between consecutive columns of the
+// tile; block-Jacobi at tile ends, as the single-RHS chunks).  Diagonal:
+// lam1 a + lam2 deg (+ X_j^T X_j for PC_TRIDIAG); couplings -lam2 w.
+__device__ __forceinline__ void tile_factor(const BatchParams& P, long long k, long long j0, int len) {
+  const long long base = k * P.p + j0;
+  double prev_d = 1.0, prev_c = 0.0;
+  for (int i = 0; i < len; ++i) {
+    const long long o = base + i;
+    double dd = P.la[o] + ((P.wl[o] + P.wr[o]) + (P.wu[o] + P.wd[o]));
+    if (P.precond == PC_TRIDIAG) dd += P.d[j0 + i];
+    double m = 0.0;
+    if (i > 0) {
+      m = -P.wl[o] / prev_d;
+      dd = fma(-m, prev_c, dd);
+    }
+    P.lmul[o] = m;
+    P.dinv[o] = 1.0 / dd;
+    prev_d = dd;
+    prev_c = (i + 1 < len) ? -P.wr[o] : 0.0;
+  }
+}
+
+// z = M^-1 r on one tile for RHS k (forward and back substitution); writes z
+// (and p = z when `pz` is given); returns the tile's sum of r z.
+__device__ __forceinline__ double tile_solve(const BatchParams& P, long long k, long long j0, int len,
+                                             double* pz) {
+  const long long base = k * P.p + j0;
+  double y = 0.0;
+  for (int i = 0; i < len; ++i) {
+    const long long o = base + i;
+    y = fma(-P.lmul[o], y, P.r[o]);
+    P.z[o] = y;                               // forward result, overwritten below
+  }
+  double zn = 0.0, rz = 0.0;
+  for (int i = len - 1; i >= 0; --i) {
+    const long long o = base + i;
+    const double c = (i + 1 < len) ? -P.wr[o] : 0.0;
+    const double z = fma(-c, zn, P.z[o]) * P.dinv[o];
+    P.z[o] = z;
+    if (pz) pz[o] = z;
+    rz = fma(P.r[o], z, rz);
+    zn = z;
+  }
+  return rz;
+}
+
 __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
   extern __shared__ __align__(1024) unsigned char smb[];
   const int tid = threadIdx.x;
@@ -304,63 +355,98 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         wadd(&s_pen[kNRMax + k], v_pen2);
       }
     }
-    // ---------------- FP64 refinement pass 1: U0 = X b (CUDA cores, FP64)
-    for (long long it = b; it < mtiles * P.S; it += G) {
-      const long long mt = it % mtiles, sp = it / mtiles;
-      const long long jb = sp * P.kchunk, je = jb + P.kchunk < p ? jb + P.kchunk : p;
-      const int row = tid % kTM, h = tid / kTM;       // 2 halves of 32 RHS
-      const long long i = mt * kTM + row;
-      double acc[32];
-#pragma unroll
-      for (int m = 0; m < 32; ++m) acc[m] = 0.0;
-      for (long long j0 = jb; j0 < je; j0 += 64) {
-        __syncthreads();
-        for (int e = tid; e < 64 * kNRMax; e += kBT) {
-          const int jj = e / kNRMax, k = e % kNRMax;
-          const long long j = j0 + jj;
-          b64[jj * kNRMax + k] = (k < K && s_act[k] && j < je) ? ldcg(P.x + (long long)k * p + j) : 0.0;
-        }
-        __syncthreads();
-        const int jn = (int)(je - j0 < 64 ? je - j0 : 64);
-        if (i < n) {
-          for (int jj = 0; jj < jn; ++jj) {
-            const double xv = (double)__bfloat162float(P.Xt[(j0 + jj) * P.ldn + i]);
-            const double* bb = b64 + jj * kNRMax + h * 32;
-#pragma unroll
-            for (int m = 0; m < 32; ++m) acc[m] = fma(xv, bb[m], acc[m]);
+    if (P.precond != PC_JACOBI) {
+      __syncthreads();
+      for (long long t = b; t < ntiles; t += G)
+        if (tid < K && s_act[tid])
+          tile_factor(P, tid, t * kTM, (int)(p - t * kTM < kTM ? p - t * kTM : kTM));
+    }
+    // ---------------- objective and outer stop.  u0 = X b and X^T X b are
+    // recomputed exactly in FP64 every refine_every MM iterations and whenever
+    // a right-hand side would otherwise stop; in between they are advanced from
+    // the CG iterations' own products (FP64 accumulation of FP32-accurate terms).
+    bool exact = (mm % P.refine_every) == 0;
+    bool pen_done = false;
+    while (true) {
+      if (exact) {
+        // FP64 refinement pass 1: U0 = X b (CUDA cores, FP64)
+        for (long long it = b; it < mtiles * P.S; it += G) {
+          const long long mt = it % mtiles, sp = it / mtiles;
+          const long long jb = sp * P.kchunk, je = jb + P.kchunk < p ? jb + P.kchunk : p;
+          const int row = tid % kTM, h = tid / kTM;       // 2 halves of 32 RHS
+          const long long i = mt * kTM + row;
+          double acc[32];
+          #pragma unroll
+          for (int m = 0; m < 32; ++m) acc[m] = 0.0;
+          for (long long j0 = jb; j0 < je; j0 += 64) {
+            __syncthreads();
+            for (int e = tid; e < 64 * kNRMax; e += kBT) {
+              const int jj = e / kNRMax, k = e % kNRMax;
+              const long long j = j0 + jj;
+              b64[jj * kNRMax + k] = (k < K && s_act[k] && j < je) ? ldcg(P.x + (long long)k * p + j) : 0.0;
+            }
+            __syncthreads();
+            const int jn = (int)(je - j0 < 64 ? je - j0 : 64);
+            if (i < n) {
+              for (int jj = 0; jj < jn; ++jj) {
+                const double xv = (double)__bfloat162float(P.Xt[(j0 + jj) * P.ldn + i]);
+                const double* bb = b64 + jj * kNRMax + h * 32;
+                #pragma unroll
+                for (int m = 0; m < 32; ++m) acc[m] = fma(xv, bb[m], acc[m]);
+              }
+            }
+          }
+          if (i < n) {
+            #pragma unroll
+            for (int m = 0; m < 32; ++m) {
+              const int k = h * 32 + m;
+              if (k < NR) P.U0part[((long long)sp * NR + k) * n + i] = acc[m];
+            }
           }
         }
       }
-      if (i < n) {
-#pragma unroll
-        for (int m = 0; m < 32; ++m) {
-          const int k = h * 32 + m;
-          if (k < NR) P.U0part[((long long)sp * NR + k) * n + i] = acc[m];
+      __syncthreads();
+      if (!pen_done) {
+        if (!grid_red(s_pen, s_pen, 2 * kNRMax)) { alive = false; break; }
+        pen_done = true;
+      } else if (!gb.sync()) { alive = false; break; }
+      // U0 (exact: sum of the split partials) and the residual sum of squares
+      for (int f = tid; f < kNRMax; f += kBT) s_rss[f] = 0.0;
+      __syncthreads();
+      {
+        const long long rows_per = (n + G - 1) / G;
+        const long long i0 = (long long)b * rows_per, i1 = i0 + rows_per < n ? i0 + rows_per : n;
+        for (long long e = tid; e < (long long)K * (i1 > i0 ? i1 - i0 : 0); e += kBT) {
+          const int k = (int)(e / (i1 - i0));
+          const long long i = i0 + e % (i1 - i0);
+          if (!s_act[k]) continue;
+          double sv;
+          if (exact) {
+            sv = 0.0;
+            for (int sp = 0; sp < P.S; ++sp) sv += ldcg(P.U0part + ((long long)sp * NR + k) * n + i);
+            P.U0[(long long)k * n + i] = sv;
+          } else {
+            sv = P.U0[(long long)k * n + i];
+          }
+          const double rr = P.y[i] - sv;
+          atomicAdd(&s_rss[k], rr * rr);
         }
       }
-    }
-    __syncthreads();
-    if (!grid_red(s_pen, s_pen, 2 * kNRMax)) { alive = false; break; }
-    // ---------------- reduce U0 over the split chunks; residual sum of squares
-    for (int f = tid; f < kNRMax; f += kBT) s_rss[f] = 0.0;
-    __syncthreads();
-    {
-      const long long rows_per = (n + G - 1) / G;
-      const long long i0 = (long long)b * rows_per, i1 = i0 + rows_per < n ? i0 + rows_per : n;
-      for (long long e = tid; e < (long long)K * (i1 > i0 ? i1 - i0 : 0); e += kBT) {
-        const int k = (int)(e / (i1 - i0));
-        const long long i = i0 + e % (i1 - i0);
-        if (!s_act[k]) continue;
-        double s = 0.0;
-        for (int sp = 0; sp < P.S; ++sp) s += ldcg(P.U0part + ((long long)sp * NR + k) * n + i);
-        P.U0[(long long)k * n + i] = s;
-        const double rr = P.y[i] - s;
-        atomicAdd(&s_rss[k], rr * rr);
+      __syncthreads();
+      if (!grid_red(s_rss, s_rss, kNRMax)) { alive = false; break; }
+      // f(beta_k) (Eq. obj); a tracked value that passes the stop test is re-checked exactly
+      if (tid == 0) s_rz[0] = 0.0;
+      __syncthreads();
+      if (tid < K && s_act[tid]) {
+        const int k = tid;
+        const double fk = 0.5 * s_rss[k] + P.lam1[k] * s_pen[k] + P.lam2[k] * s_pen[kNRMax + k];
+        if (!exact && s_mm[k] > 0 && fabs(fk - s_fp[k]) <= P.tol * fabs(s_fp[k])) s_rz[0] = 1.0;
       }
+      __syncthreads();
+      if (!exact && s_rz[0] != 0.0) { exact = true; __syncthreads(); continue; }
+      break;
     }
-    __syncthreads();
-    if (!grid_red(s_rss, s_rss, kNRMax)) { alive = false; break; }
-    // ---------------- objective f(beta_k) (Eq. obj) and the outer stop per RHS
+    if (!alive) break;
     if (tid < K) {
       const int k = tid;
       if (s_act[k]) {
@@ -381,7 +467,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
     // ---------------- FP64 refinement pass 2: r0 = c - X^T U0 - S b; z0; p1 = z0
     for (int f = tid; f < kNRMax; f += kBT) { s_rz[f] = 0.0; s_rr[f] = 0.0; }
     __syncthreads();
-    for (long long t = b; t < ntiles; t += G) {
+    for (long long t = b; exact && t < ntiles; t += G) {
       const int cl = tid % kTM, h = tid / kTM;
       const long long j = t * kTM + cl;
       double acc[32];
@@ -425,13 +511,24 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
           if (j < p) {
             const long long o = (long long)k * p + j;
             const double rj = (P.c[j] - P.t0[o]) - P.q[o];
-            const double zj = rj * P.idg[o];
-            P.r[o] = rj; P.z[o] = zj; pc[o] = zj;
-            v_rz = rj * zj;
+            P.r[o] = rj;
             v_rr = rj * rj;
+            if (P.precond == PC_JACOBI) {
+              const double zj = rj * P.idg[o];
+              P.z[o] = zj; pc[o] = zj;
+              v_rz = rj * zj;
+            }
           }
-          wadd(&s_rz[k], v_rz);
+          if (P.precond == PC_JACOBI) wadd(&s_rz[k], v_rz);
           wadd(&s_rr[k], v_rr);
+        }
+        if (P.precond != PC_JACOBI) {
+          __syncthreads();
+          if (tid < K && s_act[tid]) {
+            const double rz = tile_solve(P, tid, t * kTM, (int)(p - t * kTM < kTM ? p - t * kTM : kTM), pc);
+            atomicAdd(&s_rz[tid], rz);
+          }
+          __syncthreads();
         }
       }
     }
@@ -539,6 +636,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
             for (int sp = 0; sp < P.S; ++sp) s += (double)ldcg(P.Upart + ((long long)sp * NR + k) * n + i);
           __nv_bfloat16 h, m, l;
           split3(s, h, m, l);
+          if (i < n) P.Uf[(long long)k * n + i] = (float)s;
           P.Us[(0LL * NR + k) * P.ldn + i] = h;
           P.Us[(1LL * NR + k) * P.ldn + i] = m;
           P.Us[(2LL * NR + k) * P.ldn + i] = l;
@@ -561,6 +659,19 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         s_nu[k] = nu;
       }
       __syncthreads();
+      // tracked u0 += nu U for this block's row slice (same slicing as (c))
+      {
+        const long long rows_per = (P.ldn + G - 1) / G;
+        const long long i0 = (long long)b * rows_per;
+        const long long i1 = i0 + rows_per < n ? i0 + rows_per : n;
+        const long long cnt = i1 > i0 ? i1 - i0 : 0;
+        for (long long e = tid; e < (long long)K * cnt; e += kBT) {
+          const int k = (int)(e / cnt);
+          const long long i = i0 + e % cnt;
+          if (s_cga[k]) P.U0[(long long)k * n + i] = fma(s_nu[k], (double)P.Uf[(long long)k * n + i],
+                                                        P.U0[(long long)k * n + i]);
+        }
+      }
       // (d) phase C: T = X^T U for the owned tiles (tensor cores), then the updates
       double* loc = s_pen;   // 2*kNRMax partials: r^T z, r^T r
       for (int f = tid; f < 2 * kNRMax; f += kBT) loc[f] = 0.0;
@@ -578,19 +689,28 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
           if (j < p) {
             const long long o = (long long)k * p + j;
             const double nu = s_nu[k];
-            const double qj = (double)ts[k * kTM + cl] + P.q[o];
+            const double tj = (double)ts[k * kTM + cl];
+            P.t0[o] = fma(nu, tj, P.t0[o]);           // tracked X^T X x
+            const double qj = tj + P.q[o];
             P.x[o] = fma(nu, pc[o], P.x[o]);
             const double rj = fma(-nu, qj, P.r[o]);
-            const double zj = rj * P.idg[o];
             P.r[o] = rj;
-            P.z[o] = zj;
-            v_rz = rj * zj;
             v_rr = rj * rj;
+            if (P.precond == PC_JACOBI) {
+              const double zj = rj * P.idg[o];
+              P.z[o] = zj;
+              v_rz = rj * zj;
+            }
           }
-          wadd(&loc[k], v_rz);
+          if (P.precond == PC_JACOBI) wadd(&loc[k], v_rz);
           wadd(&loc[kNRMax + k], v_rr);
         }
         __syncthreads();
+        if (P.precond != PC_JACOBI) {
+          if (tid < K && s_cga[tid])
+            atomicAdd(&loc[tid], tile_solve(P, tid, t * kTM, rows, nullptr));
+          __syncthreads();
+        }
       }
       if (!alive) break;
       if (!grid_red(loc, loc, 2 * kNRMax)) { alive = false; break; }

@@ -95,8 +95,10 @@ struct GridBarrier {
     if (threadIdx.x == 0) {
       epoch += 1;
       const unsigned target = epoch * gridDim.x;
-      __threadfence();
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
+      // the block's writes (ordered before this thread by __syncthreads) are
+      // released to the GPU scope, then the arrival is counted
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
       int ok = 1;
       const long long t0 = clock64();
       unsigned spins = 0;
@@ -114,8 +116,7 @@ struct GridBarrier {
           }
         }
       }
-      __threadfence();
-      s_ok = ok;
+      s_ok = ok;   // the acquire loads above order the reads that follow the barrier
     }
     __syncthreads();
     return s_ok != 0;
@@ -123,42 +124,13 @@ struct GridBarrier {
 };
 
 // ---------------------------------------------------------------------------
-// Deterministic reductions (fixed shuffle pattern, fixed warp order).
+// Deterministic warp reduction (fixed shuffle pattern).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-// Sum NF doubles over the first `nw` warps of the block (warps >= nw must
-// pass zeros or not hold data); every thread returns the totals.
-// `rs` is kWarps*NF + NF doubles of shared memory.
-template <int NF>
-__device__ __forceinline__ void block_sum(double (&v)[NF], double* rs, int nw) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp < nw) {
-#pragma unroll
-    for (int f = 0; f < NF; ++f) v[f] = warp_sum(v[f]);
-    if (lane == 0) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f) rs[warp * NF + f] = v[f];
-    }
-  }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      double s = lane < nw ? rs[lane * NF + f] : 0.0;
-      s = warp_sum(s);
-      if (lane == 0) rs[kWarps * NF + f] = s;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int f = 0; f < NF; ++f) v[f] = rs[kWarps * NF + f];
-  __syncthreads();
 }
 
 }  // namespace flr

@@ -127,7 +127,14 @@ flr_status run(const SolveParams& P0, const void* Xt, const double* y, long long
   SolveParams P = P0;
   P.cnorm = cn > 0.0 ? cn : 1.0;
   auto kern = mm_solve_kernel<TX, GK_STENCIL>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  // per-kernel attribute shared with concurrent callers: always the device maximum
+  int dev = 0, smem_max = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return FLR_ECUDA;
+  }
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess) {
     (void)cudaGetLastError();
     return FLR_ECUDA;
   }
@@ -172,8 +179,12 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0)
     return FLR_EINVAL;
   int precond = o.precond;
-  if (precond == FLR_PC_AUTO) precond = E->kind == FLR_E_CHAIN ? FLR_PC_TRIDIAG : FLR_PC_JACOBI;
-  if (precond != FLR_PC_JACOBI && precond != FLR_PC_TRIDIAG && precond != FLR_PC_PAPER) return FLR_EINVAL;
+  if (precond == FLR_PC_AUTO) precond = E->kind == FLR_E_CHAIN ? FLR_PC_TRIDIAG : FLR_PC_TWOLEVEL;
+  if (precond != FLR_PC_JACOBI && precond != FLR_PC_TRIDIAG && precond != FLR_PC_PAPER &&
+      precond != FLR_PC_TWOLEVEL)
+    return FLR_EINVAL;
+  const bool tri = precond == FLR_PC_TRIDIAG || precond == FLR_PC_PAPER;
+  const bool two = precond == FLR_PC_TWOLEVEL;
 
   int dev = 0, sm_count = 0, smem_max = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { (void)cudaGetLastError(); return FLR_ECUDA; }
@@ -198,9 +209,11 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   const size_t o_ctl = off;  off += 256;
   const size_t o_part = off; off += up256(sizeof(double) * 2 * kNF * kMaxGridNA);
   const size_t o_cn = off;   off += 256;
-  const size_t o_vec = off;  off += 9 * vecb;                       // x r z pb0 pb1 q c d binv
+  const size_t o_vec = off;  off += 7 * vecb;                       // x z pb0 pb1 c d binv
+  const size_t o_two = off;                                          // qcinv qc qci sc0 sc1 uf cmap cid
+  if (two) off += 8 * vecb;
   const size_t o_k = off;
-  if (precond != FLR_PC_JACOBI) off += 2 * up256(sizeof(double) * (size_t)levels * (size_t)p);
+  if (tri) off += 2 * up256(sizeof(double) * (size_t)levels * (size_t)p);
   const size_t o_u = off;    off += 2 * up256(sizeof(double) * (size_t)ldn * kUR);
   if (off > (size_t)FLR_NOALLOC_SCRATCH_BYTES) return FLR_ESCRATCH;
   if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
@@ -209,8 +222,8 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   flr_status s = scratch_on(dev, &S);
   if (s != FLR_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  double* vec[9];
-  for (int i = 0; i < 9; ++i) vec[i] = reinterpret_cast<double*>(S + o_vec + i * vecb);
+  double* vec[7];
+  for (int i = 0; i < 7; ++i) vec[i] = reinterpret_cast<double*>(S + o_vec + i * vecb);
   double* ub0 = reinterpret_cast<double*>(S + o_u);
   double* ub1 = reinterpret_cast<double*>(S + o_u + up256(sizeof(double) * (size_t)ldn * kUR));
 
@@ -225,7 +238,7 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
 
   SolveParams P{};
   P.Xt = Xt; P.n = n; P.p = p; P.ldn = ldn;
-  P.y = y; P.c = vec[6]; P.d = vec[7];
+  P.y = y; P.c = vec[4]; P.d = vec[5];
   P.q2 = q2;
   P.rowptr = nullptr; P.col = nullptr;
   P.lam1 = lambda1; P.lam2 = lambda2; P.eps = eps; P.tol = tol;
@@ -233,10 +246,19 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   P.max_mm = o.max_mm; P.max_cg = o.max_cg; P.min_cg = o.min_cg; P.precond = precond;
   P.w = w; P.wpad = wpad; P.levels = levels;
   P.beta_init = nullptr;
-  P.x = vec[0]; P.r = vec[1]; P.z = vec[2]; P.pb0 = vec[3]; P.pb1 = vec[4]; P.q = vec[5];
-  P.binv = vec[8];
-  P.K1 = precond != FLR_PC_JACOBI ? reinterpret_cast<double*>(S + o_k) : nullptr;
-  P.K2 = precond != FLR_PC_JACOBI
+  P.x = vec[0]; P.z = vec[1]; P.pb0 = vec[2]; P.pb1 = vec[3];
+  P.binv = vec[6];
+  if (two) {
+    double* t[5];
+    for (int i = 0; i < 5; ++i) t[i] = reinterpret_cast<double*>(S + o_two + i * vecb);
+    P.qcinv = t[0]; P.qc = t[1]; P.qci = t[2]; P.sc0 = t[3]; P.sc1 = t[4];
+    P.uf = reinterpret_cast<int*>(S + o_two + 5 * vecb);
+    P.cmap = reinterpret_cast<int*>(S + o_two + 6 * vecb);
+    P.cid = reinterpret_cast<int*>(S + o_two + 7 * vecb);
+    P.ncomp = reinterpret_cast<int*>(S + o_ctl + 96);
+  }
+  P.K1 = tri ? reinterpret_cast<double*>(S + o_k) : nullptr;
+  P.K2 = tri
              ? reinterpret_cast<double*>(S + o_k + up256(sizeof(double) * (size_t)levels * (size_t)p))
              : nullptr;
   P.ub0 = ub0; P.ub1 = ub1;
@@ -250,10 +272,10 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   const auto t0 = std::chrono::steady_clock::now();
   double* cnorm_dev = reinterpret_cast<double*>(S + o_cn);
   switch (dtype) {
-    case FLR_F64: s = run<double>(P, Xt, y, n, p, ldn, (int)G, smem, sm_count, st, cnorm_dev, vec[7], vec[6]); break;
-    case FLR_F32: s = run<float>(P, Xt, y, n, p, ldn, (int)G, smem, sm_count, st, cnorm_dev, vec[7], vec[6]); break;
-    case FLR_BF16: s = run<__nv_bfloat16>(P, Xt, y, n, p, ldn, (int)G, smem, sm_count, st, cnorm_dev, vec[7], vec[6]); break;
-    case FLR_F16: s = run<__half>(P, Xt, y, n, p, ldn, (int)G, smem, sm_count, st, cnorm_dev, vec[7], vec[6]); break;
+    case FLR_F64: s = run<double>(P, Xt, y, n, p, ldn, (int)G, smem, sm_count, st, cnorm_dev, vec[5], vec[4]); break;
+    case FLR_F32: s = run<float>(P, Xt, y, n, p, ldn, (int)G, smem, sm_count, st, cnorm_dev, vec[5], vec[4]); break;
+    case FLR_BF16: s = run<__nv_bfloat16>(P, Xt, y, n, p, ldn, (int)G, smem, sm_count, st, cnorm_dev, vec[5], vec[4]); break;
+    case FLR_F16: s = run<__half>(P, Xt, y, n, p, ldn, (int)G, smem, sm_count, st, cnorm_dev, vec[5], vec[4]); break;
     default: return FLR_EINVAL;
   }
   if (s != FLR_OK) return s;

@@ -33,6 +33,23 @@
 // recomputed as z_k + gamma p_old_k from double-buffered p, bit-identical
 // to the owner's own update.
 //
+// Two-level preconditioner (PC_TWOLEVEL).  Fused neighbours (|b_j - b_k|
+// near 0) couple with lam2 w_jk ~ lam2 / eps, far above d_j + lam1 a_j, and
+// every connected group of such strong couplings leaves Q with a tiny
+// eigenvalue along the group's constant vector, which Jacobi does not see.
+// The preconditioner adds a coarse correction on exactly those directions:
+//   M^-1 r = D^-1 r + sum_c 1_c (1_c^T r) / q_c,      D = diag(Q),
+//   q_c = sum_{j in c} (d_j + lam1 a_j) + sum of lam2 w_e over edges e
+//         leaving c,
+// i.e. the diagonal of P^T Q P for the piecewise-constant P of the groups,
+// with ||X 1_c||^2 replaced by sum_{j in c} d_j.  M^-1 is SPD for any
+// partition.  An edge is strong when lam2 w_jk >= kStrong * min(d_j +
+// lam1 a_j, d_k + lam1 a_k); the groups (components of size >= 2 of the
+// strong edges) come from a lock-free union-find, once per MM iteration.
+// Per CG iteration the component sums 1_c^T r are accumulated by atomics
+// before barrier 2, and every block adds sum_c (1_c^T r)^2 / q_c to r^T z
+// itself after it, so the CG iteration keeps two grid barriers.
+//
 // FP64 arithmetic is scarce on this GPU, so scalar work runs in one thread
 // and block reductions go through shared memory and a single warp.
 #pragma once
@@ -45,12 +62,18 @@ struct DevStats {
   double f, f_eps, rel_change, cg_relres;
 };
 
-enum PrecondKind : int { PC_JACOBI = 1, PC_TRIDIAG = 2, PC_PAPER = 3 };
+enum PrecondKind : int { PC_JACOBI = 1, PC_TRIDIAG = 2, PC_PAPER = 3, PC_TWOLEVEL = 4 };
 enum GraphKind : int { GK_STENCIL = 0, GK_CSR = 1 };
 enum SolveStatus : int {
   ST_OK = 0, ST_NOTCONV = 4, ST_BREAKDOWN = 5, ST_NONFINITE = 6, ST_TIMEOUT = 7
 };
-enum NbrBits : unsigned char { NB_L = 1, NB_R = 2, NB_U = 4, NB_D = 8 };
+// neighbour flags of a coefficient; the high bits mark strong edges (PC_TWOLEVEL;
+// edge lists use NB_SR for "has a strong edge")
+enum NbrBits : unsigned char {
+  NB_L = 1, NB_R = 2, NB_U = 4, NB_D = 8, NB_SL = 16, NB_SR = 32, NB_SU = 64, NB_SD = 128
+};
+constexpr unsigned char NB_STRONG = NB_SL | NB_SR | NB_SU | NB_SD;
+constexpr double kStrong = 16.0;   // strong-edge threshold of PC_TWOLEVEL
 
 constexpr int kRF = 2;   // fields per block reduction
 constexpr int kUR = 1;   // replicas of each u accumulator: block b adds into replica b % kUR,
@@ -72,7 +95,16 @@ struct SolveParams {
   int levels;                // PCR levels for the block chunk
   const double* beta_init;   // nullptr -> X_j^T y / X_j^T X_j
   // state
-  double *x, *r, *z, *pb0, *pb1, *q, *a, *wL, *wR, *wU, *wD, *wc, *idg, *K1, *K2, *binv;
+  double *x, *z, *pb0, *pb1, *wc, *K1, *K2, *binv;
+  // two-level preconditioner (p entries each; "compact" arrays are indexed by
+  // component id, ids < p)
+  int* uf;                   // union-find parent of each coefficient
+  int* cmap;                 // compact id of each component root
+  int* cid;                  // compact id of each coefficient's component, -1 outside any
+  int* ncomp;                // number of components of this MM iteration
+  double* qcinv;             // 1 / q_c of each coefficient's component (0 outside)
+  double *qc, *qci;          // compact: q_c and 1 / q_c
+  double *sc0, *sc1;         // compact: component sums of r (alternate CG iterations)
   void* ub0;                 // two accumulators, each kUR replicas of ldn doubles
   void* ub1;                 // (replica r at byte offset 8 * r * ldn; also used as floats)
   double* part;              // [2 slots][kNF][gridDim.x]
@@ -86,8 +118,8 @@ struct SolveParams {
 // shared-memory bytes of mm_solve_kernel (the host uses the same formula)
 __host__ __device__ inline size_t solve_smem_bytes(long long ldn, long long wpad, int V) {
   return (size_t)ldn * 8 + (size_t)wpad * 8 + (size_t)kThreads * V * 8 + (size_t)wpad * 8 +
-         6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 + 5 * (size_t)wpad * 8 +
-         ((size_t)kRF * kThreads + 16) * 8 + (size_t)wpad;
+         6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 +
+         ((size_t)kRF * kThreads + 16) * 8 + (size_t)wpad * 4 + (size_t)wpad;
 }
 
 template <typename TX, typename A>
@@ -312,7 +344,7 @@ __device__ __forceinline__ void apply_precond(const SolveParams& P, long long j0
                                               const double* sidg, const double* rsm,
                                               double* zsm, double* w0, double* w1) {
   const int tid = threadIdx.x;
-  if (P.precond == PC_JACOBI) {
+  if (P.precond == PC_JACOBI || P.precond == PC_TWOLEVEL) {
     for (int jj = tid; jj < wl; jj += kThreads) {
       const double z = rsm[jj] * sidg[jj];
       zsm[jj] = z;
@@ -385,6 +417,54 @@ __device__ __forceinline__ double stage_u(const A* __restrict__ u, A* us, long l
   return acc;
 }
 
+// ---- union-find over the strong edges (PC_TWOLEVEL): lock-free hooking of
+// the larger root under the smaller one by CAS, with path halving (the
+// ECL-CC scheme, Jaiganesh and Burtscher 2018).  Parent pointers never
+// increase (par[x] <= x), so every walk ends within x + 1 steps.
+__device__ __forceinline__ int vld(const int* a) { return *reinterpret_cast<const volatile int*>(a); }
+__device__ __forceinline__ void vst(int* a, int v) { *reinterpret_cast<volatile int*>(a) = v; }
+
+__device__ __forceinline__ int uf_root(int* par, int x, bool halve) {
+  int cur = x;
+  for (int it = 0; it <= x; ++it) {
+    const int pc = vld(par + cur);
+    if (pc == cur) break;
+    const int gp = vld(par + pc);
+    if (halve && gp != pc) vst(par + cur, gp);
+    cur = gp;
+  }
+  return cur;
+}
+
+// merge the components of a and b; each failed CAS lowers the larger root,
+// so the loop ends within `bound` rounds
+__device__ __forceinline__ void uf_union(int* par, int a, int b, long long bound) {
+  a = uf_root(par, a, true);
+  b = uf_root(par, b, true);
+  for (long long it = 0; a != b && it <= bound; ++it) {
+    if (a < b) { const int t = a; a = b; b = t; }
+    const int old = atomicCAS(par + a, a, b);
+    if (old == a) return;
+    a = uf_root(par, old, true);
+    b = uf_root(par, b, true);
+  }
+}
+
+// acc[key] += v over the lanes with key >= 0, one atomic per distinct key of
+// the warp.  All 32 lanes must call it.
+__device__ __forceinline__ void warp_add_by_key(double* acc, int key, double v) {
+  const int lane = threadIdx.x & 31;
+  unsigned pend = __ballot_sync(0xffffffffu, key >= 0);
+  while (pend) {
+    const int l = __ffs(pend) - 1;
+    const int k = __shfl_sync(0xffffffffu, key, l);
+    const bool mine = key == k;
+    const double s = warp_sum(mine ? v : 0.0);
+    if (lane == l) atomicAdd(acc + k, s);
+    pend &= ~__ballot_sync(0xffffffffu, mine);
+  }
+}
+
 __device__ __forceinline__ double edge_w(double xj, double xk, double eps) {
   return 1.0 / (fabs(xj - xk) + eps);
 }
@@ -410,9 +490,10 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   double* tv = redd + (long long)kThreads * V;              // wpad: X^T u per column
   double* pw = tv + wp;                                     // 6*wpad: PCR work
   double* cst = pw + 6 * wp;                                // 6*wpad: per-column constants
-  double* own = cst + 6 * wp;                               // 5*wpad: own CG vectors
-  double* rs = own + 5 * wp;                                // kRF*kThreads + 16
-  unsigned char* nb = reinterpret_cast<unsigned char*>(rs + kRF * kThreads + 16);  // wpad
+  double* own = cst + 6 * wp;                               // 6*wpad: own CG vectors
+  double* rs = own + 6 * wp;                                // kRF*kThreads + 16
+  int* cid_s = reinterpret_cast<int*>(rs + kRF * kThreads + 16);                  // wpad
+  unsigned char* nb = reinterpret_cast<unsigned char*>(cid_s + wp);               // wpad
   double* s_la = cst;            // lam1 a_j
   double* s_wl = cst + wp;       // lam2 w(j-1, j) etc.
   double* s_wr = cst + 2 * wp;
@@ -424,6 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   double* zs = own + 2 * wp;     // z (also global: halo of p)
   double* ps = own + 3 * wp;     // p (also global, double-buffered)
   double* qs = own + 4 * wp;     // S p  (S x at the CG start)
+  double* qi_s = own + 5 * wp;   // 1 / q_c of the coefficient's component (PC_TWOLEVEL)
   double* sc = rs + kRF * kThreads + 8;   // scalar broadcast slots
   Acc* us = reinterpret_cast<Acc*>(usd);
   Acc* vs = reinterpret_cast<Acc*>(vsd);
@@ -457,6 +539,8 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       for (long long i = zs0 + tid; i < ze0; i += kThreads) u[(long long)r * P.ldn + i] = 0.0;
   };
   const int rep = b % kUR;   // this block's accumulator replica
+  const bool two = P.precond == PC_TWOLEVEL;
+  const int lane = tid & 31, warp = tid >> 5;
 
   // ---- initialisation (Algorithm 1): beta_j = X_j^T y / X_j^T X_j
   for (int jj = tid; jj < wl; jj += kThreads) {
@@ -505,7 +589,22 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
         deg = (wl_ + wr_) + (wu_ + wd_);
         s_wl[jj] = P.lam2 * wl_; s_wr[jj] = P.lam2 * wr_;
         s_wu[jj] = P.lam2 * wu_; s_wd[jj] = P.lam2 * wd_;
+        if (two) {   // strong edges: the same test, with the same operands, at both ends
+          const double dlj = fma(P.lam1, aj, P.d[j]);
+          auto strong = [&](double lw, long long kk, double xk) {
+            return lw >= kStrong * fmin(dlj, fma(P.lam1, 1.0 / (fabs(xk) + P.eps), P.d[kk]));
+          };
+          unsigned char sb = fl & 15;
+          if ((fl & NB_L) && strong(s_wl[jj], j - 1, xl)) sb |= NB_SL;
+          if ((fl & NB_R) && strong(s_wr[jj], j + 1, xr)) sb |= NB_SR;
+          if ((fl & NB_U) && strong(s_wu[jj], j - q2, xu)) sb |= NB_SU;
+          if ((fl & NB_D) && strong(s_wd[jj], j + q2, xd)) sb |= NB_SD;
+          nb[jj] = sb;
+          P.uf[j] = (int)j;
+        }
       } else {
+        const double dlj = fma(P.lam1, aj, P.d[j]);
+        bool any_strong = false;
         for (long long e = P.rowptr[j]; e < P.rowptr[j + 1]; ++e) {
           const long long k = P.col[e];
           const double xk = ldcg(P.x + k);
@@ -514,6 +613,12 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
           deg += we;
           lap = fma(we, xj - xk, lap);
           if (k > j) pen[1] += fabs(xj - xk);
+          if (two && P.lam2 * we >= kStrong * fmin(dlj, fma(P.lam1, 1.0 / (fabs(xk) + P.eps), P.d[k])))
+            any_strong = true;
+        }
+        if (two) {
+          nb[jj] = any_strong ? NB_SR : 0;
+          P.uf[j] = (int)j;
         }
       }
       pen[0] += fabs(xj);
@@ -527,7 +632,8 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       xs[jj] = xj;
     }
     __syncthreads();
-    if (P.precond != PC_JACOBI && GK == GK_STENCIL) setup_tridiag(P, j0, wl, tv, s_wl, s_wr, pw);
+    if ((P.precond == PC_TRIDIAG || P.precond == PC_PAPER) && GK == GK_STENCIL)
+      setup_tridiag(P, j0, wl, tv, s_wl, s_wr, pw);
     // ---------------- u0 = X x in FP64 (refinement pass)
     zero_u(U1);
     phase_a<TX, double>(P, Xt, j0, wl, vsd, redd, reinterpret_cast<double*>(U0) + (long long)rep * P.ldn);
@@ -550,7 +656,97 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
     phase_c<TX, double>(P, Xt, j0, wl, usd, tv);
     for (int jj = tid; jj < wl; jj += kThreads) rsm[jj] = (P.c[j0 + jj] - tv[jj]) - qs[jj];
     __syncthreads();
+    int nc = 0;   // coarse components of this MM iteration (PC_TWOLEVEL)
+    if (two) {
+      // the compact arrays are free: their last readers finished before the
+      // grid barrier of the refinement pass.  Block ranges jointly cover [0, p).
+      for (int jj = tid; jj < wl; jj += kThreads) {
+        const long long j = j0 + jj;
+        P.qc[j] = 0.0;
+        P.sc0[j] = 0.0;
+        P.sc1[j] = 0.0;
+      }
+      if (b == 0 && tid == 0) vst(P.ncomp, 0);
+      // union over the strong edges, each from its lower end
+      for (int jj = tid; jj < wl; jj += kThreads) {
+        const long long j = j0 + jj;
+        const unsigned char fl = nb[jj];
+        if (GK == GK_STENCIL) {
+          if (fl & NB_SR) uf_union(P.uf, (int)j, (int)(j + 1), p);
+          if (fl & NB_SD) uf_union(P.uf, (int)j, (int)(j + q2), p);
+        } else if (fl & NB_SR) {   // the reweight's strong test, recomputed per edge
+          const double dlj = fma(P.lam1, 1.0 / (fabs(xs[jj]) + P.eps), P.d[j]);
+          for (long long e = P.rowptr[j]; e < P.rowptr[j + 1]; ++e) {
+            const long long kk = P.col[e];
+            if (kk < j) continue;
+            const double dlk = fma(P.lam1, 1.0 / (fabs(ldcg(P.x + kk)) + P.eps), P.d[kk]);
+            if (P.wc[e] >= kStrong * fmin(dlj, dlk)) uf_union(P.uf, (int)j, (int)kk, p);
+          }
+        }
+      }
+      if (!gb.sync()) return;
+      // roots are final: point every coefficient at its root; each root of a
+      // component of size >= 2 (exactly the coefficients with a strong edge)
+      // takes a compact id
+      for (int jj = tid; jj < wl; jj += kThreads) {
+        const long long j = j0 + jj;
+        const int r = uf_root(P.uf, (int)j, false);
+        vst(P.uf + j, r);
+        if (r == (int)j && (nb[jj] & NB_STRONG)) P.cmap[j] = atomicAdd(P.ncomp, 1);
+      }
+      if (!gb.sync()) return;
+      nc = vld(P.ncomp);
+      // labels, q_c and the component sums of r0
+      for (int base = warp * 32; base < wl; base += kThreads) {   // warp-uniform trip count
+        const int jj = base + lane;
+        int key = -1;
+        double qv = 0.0, rv = 0.0;
+        if (jj < wl) {
+          const long long j = j0 + jj;
+          const unsigned char fl = nb[jj];
+          if (fl & NB_STRONG) {
+            const int r = vld(P.uf + j);
+            const int c = (r >= 0 && r < p) ? P.cmap[r] : -1;
+            if (c >= 0 && c < nc) {
+              key = c;
+              double qv_ = s_la[jj] + P.d[j];   // plus lam2 w of the edges leaving the component
+              if (GK == GK_STENCIL) {
+                if ((fl & NB_L) && vld(P.uf + j - 1) != r) qv_ += s_wl[jj];
+                if ((fl & NB_R) && vld(P.uf + j + 1) != r) qv_ += s_wr[jj];
+                if ((fl & NB_U) && vld(P.uf + j - q2) != r) qv_ += s_wu[jj];
+                if ((fl & NB_D) && vld(P.uf + j + q2) != r) qv_ += s_wd[jj];
+              } else {
+                for (long long e = P.rowptr[j]; e < P.rowptr[j + 1]; ++e)
+                  if (vld(P.uf + P.col[e]) != r) qv_ += P.wc[e];
+              }
+              qv = qv_;
+              rv = rsm[jj];
+            }
+          }
+          cid_s[jj] = key;
+          P.cid[j] = key;
+        }
+        warp_add_by_key(P.qc, key, qv);
+        warp_add_by_key(P.sc0, key, rv);
+      }
+      if (!gb.sync()) return;
+      for (int jj = tid; jj < wl; jj += kThreads) {
+        const int c = cid_s[jj];
+        const double qi = c >= 0 ? 1.0 / ldcg(P.qc + c) : 0.0;
+        qi_s[jj] = qi;
+        P.qcinv[j0 + jj] = qi;
+      }
+      for (long long c = j0 + tid; c < j1 && c < nc; c += kThreads) P.qci[c] = 1.0 / ldcg(P.qc + c);
+      __syncthreads();
+    }
     apply_precond(P, j0, wl, s_idg, rsm, zs, pw, pw + wp);
+    if (two) {   // z0 = D^-1 r0 + coarse part
+      for (int jj = tid; jj < wl; jj += kThreads) {
+        const int c = cid_s[jj];
+        if (c >= 0) zs[jj] = fma(ldcg(P.sc0 + c), qi_s[jj], zs[jj]);
+      }
+      __syncthreads();
+    }
     double rz2[2] = {0.0, 0.0};
     {
       double* pg = pcur ? P.pb1 : P.pb0;
@@ -581,12 +777,20 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       void* Unext = ucur ? P.ub0 : P.ub1;
       const double* pc = pcur ? P.pb1 : P.pb0;
       const double* po = pcur ? P.pb0 : P.pb1;
+      // component sums of r: this iteration's accumulator and the previous one's
+      double* Scur = (k & 1) ? P.sc0 : P.sc1;
+      double* Sold = (k & 1) ? P.sc1 : P.sc0;
       // p at a neighbour: own values from shared memory; another block's value is
       // z + gamma p_old (bit-identical to its owner's update), or p itself at k = 0
       auto pval = [&](long long kk) -> double {
         if (kk >= j0 && kk < j1) return ps[kk - j0];
         if (k == 0) return ldcg(pc + kk);
-        return fma(gamma, ldcg(po + kk), ldcg(P.z + kk));
+        double zk = ldcg(P.z + kk);
+        if (two) {
+          const int c = __ldcg(P.cid + kk);
+          if (c >= 0) zk = fma(ldcg(Sold + c), ldcg(P.qcinv + kk), zk);
+        }
+        return fma(gamma, ldcg(po + kk), zk);
       };
       double sv[1] = {0.0};
       for (int jj = tid; jj < wl; jj += kThreads) {
@@ -638,6 +842,15 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       }
       __syncthreads();
       apply_precond(P, j0, wl, s_idg, rsm, zs, pw, pw + wp);
+      if (two) {
+        // 1_c^T r into this iteration's accumulator; clear the previous one (its
+        // readers, the p update and the halo of phase A, finished before barrier 1)
+        for (int base = warp * 32; base < wl; base += kThreads) {
+          const int jj = base + lane;
+          warp_add_by_key(Scur, jj < wl ? cid_s[jj] : -1, jj < wl ? rsm[jj] : 0.0);
+        }
+        for (long long c = j0 + tid; c < j1 && c < nc; c += kThreads) Sold[c] = 0.0;
+      }
       double rzn[2] = {0.0, 0.0};
       for (int jj = tid; jj < wl; jj += kThreads) {
         const double rj = rsm[jj];
@@ -646,6 +859,15 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       }
       block_reduce<2>(rzn, rs, ncol);
       if (!grid_sum(rzn)) return;
+      if (two) {   // r^T z += sum_c (1_c^T r)^2 / q_c, in the same order in every block
+        double cz[1] = {0.0};
+        for (int c = tid; c < nc; c += kThreads) {
+          const double sv_ = ldcg(Scur + c);
+          cz[0] = fma(sv_ * sv_, ldcg(P.qci + c), cz[0]);
+        }
+        block_reduce<1>(cz, rs, kThreads);
+        rzn[0] += cz[0];
+      }
       if (tid == 0) sc[4] = rzn[0] / rz;
       __syncthreads();
       gamma = sc[4];
@@ -654,7 +876,12 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       // p_{j+1} = z_j + gamma p_j (shared copy and the other global buffer)
       double* pn = pcur ? P.pb0 : P.pb1;
       for (int jj = tid; jj < wl; jj += kThreads) {
-        const double v = fma(gamma, ps[jj], zs[jj]);
+        double zj = zs[jj];
+        if (two) {
+          const int c = cid_s[jj];
+          if (c >= 0) zj = fma(ldcg(Scur + c), qi_s[jj], zj);
+        }
+        const double v = fma(gamma, ps[jj], zj);
         ps[jj] = v;
         pn[j0 + jj] = v;
       }

@@ -71,7 +71,7 @@ def assert_parity(st, beta, f_ref, beta_ref, check_beta=True):
 
 
 # --------------------------------------------------------------------------- configurations
-@pytest.mark.parametrize("precond", ["tridiag", "jacobi", "paper"])
+@pytest.mark.parametrize("precond", ["tridiag", "jacobi", "paper", "twolevel"])
 def test_config1_chain_f64(flr, precond):
     g = golden("config1")
     pr = fi.config(1)
@@ -103,7 +103,7 @@ def test_config2_lattice_f32_small(flr):
     assert_parity(st, beta, g["f"], np.array(g["beta"]))
 
 
-@pytest.mark.parametrize("precond", ["jacobi", "tridiag"])
+@pytest.mark.parametrize("precond", ["jacobi", "tridiag", "twolevel"])
 def test_config2_lattice_q40(flr, precond):
     g = golden("config2_q40")
     pr = fi.config(2, scale=0.16)
@@ -112,6 +112,19 @@ def test_config2_lattice_q40(flr, precond):
     beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-9, precond=precond,
                           tol_cg=1e-8, max_mm=20000)
     assert_parity(st, beta, g["f"], np.array(g["beta"]), check_beta=False)
+
+
+def test_twolevel_cuts_cg_iterations(flr):
+    """The coarse correction on fused groups: same answer, several times fewer CG iterations."""
+    g = golden("config2_q40")
+    pr = fi.config(2, scale=0.16)
+    prob = problem(flr, pr)
+    kw = dict(eps=pr.eps, tol=1e-9, tol_cg=1e-8, max_mm=20000)
+    bj, sj = prob.solve(pr.lam1, pr.lam2, precond="jacobi", **kw)
+    bt, st = prob.solve(pr.lam1, pr.lam2, precond="twolevel", **kw)
+    assert_parity(sj, bj, g["f"], np.array(g["beta"]), check_beta=False)
+    assert_parity(st, bt, g["f"], np.array(g["beta"]), check_beta=False)
+    assert 3 * st.cg_iters < sj.cg_iters, (st.cg_iters, sj.cg_iters)
 
 
 def test_config4_lattice_f16_small(flr):
@@ -184,12 +197,13 @@ def test_unpenalised_is_least_squares(flr):
     np.testing.assert_allclose(beta.cpu().numpy(), exact.least_squares(X, y), rtol=1e-8, atol=1e-10)
 
 
-def test_edge_list_matches_stencil(flr):
+@pytest.mark.parametrize("precond", ["jacobi", "twolevel"])
+def test_edge_list_matches_stencil(flr, precond):
     """The same lattice as an explicit edge list (CSR path) and as a stencil."""
     pr = fi.config(2, scale=0.04)
     a = problem(flr, pr)
     b = problem(flr, pr, graph={"kind": "edges", "edges": pr.graph.edges})
-    kw = dict(eps=pr.eps, tol=1e-10, tol_cg=1e-10, precond="jacobi", max_mm=20000)
+    kw = dict(eps=pr.eps, tol=1e-10, tol_cg=1e-10, precond=precond, max_mm=20000)
     ba, sa = a.solve(pr.lam1, pr.lam2, **kw)
     bb, sb = b.solve(pr.lam1, pr.lam2, **kw)
     assert abs(sa.f - sb.f) <= 1e-9 * sa.f
@@ -258,8 +272,10 @@ def test_repeat_is_deterministic(flr):
     prob = problem(flr, pr)
     b1, s1 = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-8)
     b2, s2 = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-8)
-    assert s1.mm_iters == s2.mm_iters
-    assert abs(s1.f - s2.f) <= 1e-12 * abs(s1.f)
+    # FP64 atomics (u accumulation, component sums of the two-level
+    # preconditioner) add in a run-dependent order: equal up to rounding
+    assert abs(s1.mm_iters - s2.mm_iters) <= 1
+    assert abs(s1.f - s2.f) <= 1e-10 * abs(s1.f)
 
 
 def test_notconv_and_warm_start(flr):
