@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--served-slots", type=int, default=4,
                     help="concurrent copies for the served-form measurement (0 = skip)")
     ap.add_argument("--slots", type=int, default=4)
-    ap.add_argument("--once", default=None, choices=["config2", "config4", "batch3", "serve5"],
+    ap.add_argument("--once", default=None, choices=["config2", "config4", "batch3", "chain3", "serve5"],
                     help="one solve of a workload (for profiler captures), then exit")
     ap.add_argument("--max-mm", type=int, default=20000)
     ap.add_argument("--max-cg", type=int, default=10000)
@@ -254,6 +254,27 @@ def solve_batch3(args):
     print(json.dumps(out))
 
 
+def solve_chain3(args):
+    """Three points of the batched chain workload's lambda grid (corners and middle) as
+    single solves with the chosen preconditioner."""
+    import torch
+    import flr_inputs as fi
+    import paper_1306_1970_gb300 as flr
+    flr.load(build_if_missing=True)
+    pr = fi.config(3)
+    X = torch.from_numpy(pr.X).view(torch.int16).cuda()
+    prob = flr.Problem(X, torch.from_numpy(pr.y).cuda(), pr.graph, dtype="bf16")
+    out = []
+    for k in (0, 27, 63):
+        l1, l2 = pr.lam_grid[k]
+        _, st = prob.solve(l1, l2, eps=pr.eps, tol=args.tol, tol_cg=args.tol_cg, precond=args.precond,
+                           max_mm=args.max_mm, max_cg=args.max_cg, check=False)
+        out.append({"k": k, "lam1": float(l1), "lam2": float(l2), "mm": st.mm_iters, "cg": st.cg_iters,
+                    "ms": st.ms, "f": st.f, "status": st.status,
+                    "us_per_cg": 1000.0 * st.ms / max(1, st.cg_iters)})
+    print(json.dumps({"once": "chain3", "precond": args.precond, "solves": out}))
+
+
 def serve5(args):
     """Served mixed stream: closed loop (all requests queued at once) for the capacity,
     then Poisson arrivals at 0.8 x capacity for p50/p99 latency (submit to done).
@@ -323,6 +344,8 @@ def solve_once(args):
     import paper_1306_1970_gb300 as flr
     if args.once == "batch3":
         return solve_batch3(args)
+    if args.once == "chain3":
+        return solve_chain3(args)
     if args.once == "serve5":
         return serve5(args)
     flr.load(build_if_missing=True)

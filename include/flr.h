@@ -86,16 +86,17 @@ typedef struct flr_graph {
  *                   horizontal-line preconditioner.
  *   FLR_PC_PAPER:   as TRIDIAG but without diag(X^T X): M = lambda1 A + lambda2 B
  *                   restricted to consecutive-index couplings (Algorithm 2).
- *   FLR_PC_TWOLEVEL: Jacobi plus a coarse correction on the fused groups:
- *                   M^-1 r = D^-1 r + sum_c 1_c (1_c^T r) / q_c, with D the
- *                   diagonal of Q, c running over the connected components
+ *   FLR_PC_TWOLEVEL: a local part plus a coarse correction on the fused groups:
+ *                   M^-1 r = L^-1 r + sum_c 1_c (1_c^T r) / q_c, with L the
+ *                   TRIDIAG matrix on a chain and the diagonal of Q on other
+ *                   graphs, c running over the connected components
  *                   (two or more coefficients) of the edges whose weight
  *                   lambda2 w_jk is at least 16 min(d_j + lambda1 a_j,
  *                   d_k + lambda1 a_k), 1_c their indicator vectors and q_c =
  *                   sum_{j in c}(d_j + lambda1 a_j) + the lambda2 w of the
  *                   edges leaving c.  Recomputed every MM iteration.  Any
  *                   graph kind.
- *   FLR_PC_AUTO:    TRIDIAG for chains, TWOLEVEL for lattices and edge lists. */
+ *   FLR_PC_AUTO:    TWOLEVEL (flr_solve_batch: its per-tile TRIDIAG). */
 typedef enum flr_precond {
     FLR_PC_AUTO = 0, FLR_PC_JACOBI = 1, FLR_PC_TRIDIAG = 2, FLR_PC_PAPER = 3, FLR_PC_TWOLEVEL = 4
 } flr_precond;
@@ -112,9 +113,10 @@ typedef struct flr_opts {
                             FLR_ETIMEOUT (needs grid >= 2).  0 in normal use. */
     int64_t wait_cycles; /* bound of every device-side wait in SM clock cycles (0 = 2^33) */
     int32_t refine_every;/* flr_solve_batch: X b and X^T X b are recomputed exactly in FP64 every
-                            this many MM iterations and before any problem is declared
-                            converged; in between they are advanced from the CG products
-                            (0 = 8; 1 = every iteration).  flr_solve always recomputes. */
+                            this many MM iterations, after every 128 CG iterations, and
+                            before any problem is declared converged; in between they are
+                            advanced from the CG products (0 or 1 = every MM iteration, the
+                            default).  flr_solve always recomputes. */
     int32_t reserved[3];
 } flr_opts;
 

@@ -213,16 +213,30 @@ flr_status build_csr(flr_handle* h, const int64_t* edges_host, long long m) {
   return FLR_OK;
 }
 
+// Largest dynamic shared memory a launch of `kern` may request on `dev`: the
+// per-block opt-in limit minus the kernel's static shared memory.
+cudaError_t max_dynamic_smem(const void* kern, int dev, int* out) {
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  *out = optin - (int)fa.sharedSizeBytes;
+  return cudaSuccess;
+}
+
 template <typename TX, int GK>
 flr_status launch_solve_t(flr_handle* h, SolveParams& P, int G, size_t smem) {
   auto kern = mm_solve_kernel<TX, GK>;
   // The attribute is per kernel, shared by every thread of the process: set it
-  // to the device maximum (the same value from every caller), never to this
-  // launch's size, which a concurrent solve could lower before this launch.
-  int smem_max = 0;
-  FLR_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-  if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
-  FLR_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  // to the most the device allows next to the kernel's static shared memory
+  // (the same value from every caller), never to this launch's size, which a
+  // concurrent solve could lower before this launch.
+  int dyn_max = 0;
+  FLR_TRY(max_dynamic_smem((const void*)kern, h->device, &dyn_max));
+  if (smem > (size_t)dyn_max) return FLR_ENOTIMPL;
+  FLR_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
   int nb = 0;
   FLR_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem));
   if (nb < 1 || G > nb * h->sm_count) return FLR_ENOTIMPL;
@@ -323,17 +337,17 @@ flr_status batch_group(flr_handle* h, int K, const double* l1, const double* l2,
   }
   P.Ps = h->Ps; P.Us = h->Us; P.Upart = h->Upart; P.U0part = h->U0part; P.U0 = h->U0;
   P.Uf = h->Uf;
-  P.refine_every = o.refine_every > 0 ? o.refine_every : 8;
+  P.refine_every = o.refine_every > 0 ? o.refine_every : 1;
   P.red = h->bred;
   P.bar = reinterpret_cast<unsigned*>(h->bctl);
   P.err = reinterpret_cast<int*>(h->bctl + 64);
   P.stats = h->bstats;
   P.timeout = o.wait_cycles > 0 ? o.wait_cycles : (1LL << 33);
   const size_t smem = batch_smem_bytes(NR);
-  int smem_max = 0;
-  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-  if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
-  FLR_TRY(cudaFuncSetAttribute(mm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  int dyn_max = 0;
+  FLR_TRY(max_dynamic_smem((const void*)mm_batch_kernel, h->device, &dyn_max));
+  if (smem > (size_t)dyn_max) return FLR_ENOTIMPL;
+  FLR_TRY(cudaFuncSetAttribute(mm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
   int nb = 0;
   FLR_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mm_batch_kernel, kBT, smem));
   if (nb < 1) return FLR_ENOTIMPL;
@@ -562,7 +576,7 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   if (prev_dev != h->device) cudaSetDevice(h->device);
 
   int precond = o.precond;
-  if (precond == FLR_PC_AUTO) precond = h->gkind == FLR_E_CHAIN ? FLR_PC_TRIDIAG : FLR_PC_TWOLEVEL;
+  if (precond == FLR_PC_AUTO) precond = FLR_PC_TWOLEVEL;
   if (precond != FLR_PC_JACOBI && precond != FLR_PC_TRIDIAG && precond != FLR_PC_PAPER &&
       precond != FLR_PC_TWOLEVEL)
     return FLR_EINVAL;

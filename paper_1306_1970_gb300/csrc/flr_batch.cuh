@@ -27,10 +27,14 @@ namespace flr {
 
 constexpr int kBT = 256;                 // threads per block
 constexpr int kNRMax = 64;               // right-hand sides per launch
-constexpr int kTM = 128;                 // tile rows (MMA M)
+constexpr int kTM = 128;                 // tile rows (MMA M); the element loops take 4 x 32 columns
 constexpr int kNS = 3;                   // cp.async / MMA pipeline stages
 constexpr int kSlices = 3;               // BF16 slices per FP64/FP32 operand
 constexpr int kRedSlots = 3;
+// Tracked X b and X^T X b drift with every CG step (FP32-level products), so
+// an exact FP64 pass is also forced once this many lockstep CG iterations
+// have run since the last one.
+constexpr int kTrackMaxCG = 128;
 
 struct BatchStats {
   int mm_iters, cg_iters, status, pad;
@@ -219,33 +223,75 @@ __device__ __forceinline__ void tile_factor(const BatchParams& P, long long k, l
   }
 }
 
-// z = M^-1 r on one tile for RHS k (forward and back substitution); writes z
-// (and p = z when `pz` is given); returns the tile's sum of r z.
-__device__ __forceinline__ double tile_solve(const BatchParams& P, long long k, long long j0, int len,
-                                             double* pz) {
+// z = M^-1 r on one tile for RHS k with the factors of tile_factor; writes z
+// (and p = z when `pz` is given) and returns the tile's sum of r z.  Both
+// substitutions are first-order linear
+// recurrences, y_i = -m_i y_{i-1} + r_i forward and z_i = a_i z_{i+1} + b_i
+// backward (a_i = -c_i / d_i, b_i = y_i / d_i).  Lane l holds entries
+// 4l..4l+3, composes their affine maps, a 5-step shuffle scan composes the
+// lanes, and each lane then runs its 4 entries from the incoming value.
+// All 32 lanes call; lane 0 returns the tile's sum of r z (others: the same).
+__device__ __forceinline__ double tile_solve_warp(const BatchParams& P, long long k, long long j0,
+                                                  int len, double* pz) {
+  const int lane = threadIdx.x & 31;
   const long long base = k * P.p + j0;
-  double y = 0.0;
-  for (int i = 0; i < len; ++i) {
-    const long long o = base + i;
-    y = fma(-P.lmul[o], y, P.r[o]);
-    P.z[o] = y;                               // forward result, overwritten below
+  const int i0 = lane * 4;
+  double m[4], r[4], a[4], dv[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int i = i0 + e;
+    const bool ok = i < len;
+    m[e] = ok ? P.lmul[base + i] : 0.0;
+    r[e] = ok ? P.r[base + i] : 0.0;
+    dv[e] = ok ? P.dinv[base + i] : 0.0;
+    const double c = (ok && i + 1 < len) ? -P.wr[base + i] : 0.0;
+    a[e] = -c * dv[e];
   }
-  double zn = 0.0, rz = 0.0;
-  for (int i = len - 1; i >= 0; --i) {
-    const long long o = base + i;
-    const double c = (i + 1 < len) ? -P.wr[o] : 0.0;
-    const double z = fma(-c, zn, P.z[o]) * P.dinv[o];
-    P.z[o] = z;
-    if (pz) pz[o] = z;
-    rz = fma(P.r[o], z, rz);
-    zn = z;
+  // forward: lane map y_out = A y_in + B
+  double A = 1.0, B = 0.0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) { B = fma(-m[e], B, r[e]); A = -m[e] * A; }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double Ap = __shfl_up_sync(0xffffffffu, A, o);
+    const double Bp = __shfl_up_sync(0xffffffffu, B, o);
+    if (lane >= o) { B = fma(A, Bp, B); A *= Ap; }
   }
-  return rz;
+  double y = __shfl_up_sync(0xffffffffu, B, 1);   // y before this lane's entries (y_{-1} = 0)
+  if (lane == 0) y = 0.0;
+  double b[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) { y = fma(-m[e], y, r[e]); b[e] = y * dv[e]; }
+  // backward: lane map z_in(first entry) = A z_out(after last entry) + B
+  A = 1.0; B = 0.0;
+#pragma unroll
+  for (int e = 3; e >= 0; --e) { B = fma(a[e], B, b[e]); A = a[e] * A; }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double An = __shfl_down_sync(0xffffffffu, A, o);
+    const double Bn = __shfl_down_sync(0xffffffffu, B, o);
+    if (lane + o < 32) { B = fma(A, Bn, B); A *= An; }
+  }
+  double z = __shfl_down_sync(0xffffffffu, B, 1);   // z after this lane's entries (0 past the tile)
+  if (lane == 31) z = 0.0;
+  double rz = 0.0;
+#pragma unroll
+  for (int e = 3; e >= 0; --e) {
+    z = fma(a[e], z, b[e]);
+    const int i = i0 + e;
+    if (i < len) {
+      P.z[base + i] = z;
+      if (pz) pz[base + i] = z;
+      rz = fma(r[e], z, rz);
+    }
+  }
+  return warp_sum(rz);
 }
 
 __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
   extern __shared__ __align__(1024) unsigned char smb[];
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x, b = blockIdx.x;
   const long long n = P.n, p = P.p, q2 = P.q2;
   const int K = P.K, NR = P.NR;
@@ -312,6 +358,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
   }
   bool alive = gb.sync();
   int mm = 0, pcur = 0;
+  long long cg_since_exact = 0;   // lockstep CG iterations since the last exact pass
   auto is_own = [&](long long j) -> bool { return ((j / kTM) % G) == b; };
   // In the tile loops below all 32 lanes of a warp share one RHS index k
   // (128 columns per k, a multiple of 32), so per-RHS sums reduce by warp
@@ -365,7 +412,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
     // recomputed exactly in FP64 every refine_every MM iterations and whenever
     // a right-hand side would otherwise stop; in between they are advanced from
     // the CG iterations' own products (FP64 accumulation of FP32-accurate terms).
-    bool exact = (mm % P.refine_every) == 0;
+    bool exact = (mm % P.refine_every) == 0 || cg_since_exact >= kTrackMaxCG;
     bool pen_done = false;
     while (true) {
       if (exact) {
@@ -446,6 +493,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       if (!exact && s_rz[0] != 0.0) { exact = true; __syncthreads(); continue; }
       break;
     }
+    if (exact) cg_since_exact = 0;
     if (!alive) break;
     if (tid < K) {
       const int k = tid;
@@ -524,10 +572,12 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         }
         if (P.precond != PC_JACOBI) {
           __syncthreads();
-          if (tid < K && s_act[tid]) {
-            const double rz = tile_solve(P, tid, t * kTM, (int)(p - t * kTM < kTM ? p - t * kTM : kTM), pc);
-            atomicAdd(&s_rz[tid], rz);
-          }
+          const int len = (int)(p - t * kTM < kTM ? p - t * kTM : kTM);
+          for (int k = tid >> 5; k < K; k += kBT / 32)   // one warp per RHS
+            if (s_act[k]) {
+              const double rz = tile_solve_warp(P, k, t * kTM, len, pc);
+              if ((tid & 31) == 0) atomicAdd(&s_rz[k], rz);
+            }
           __syncthreads();
         }
       }
@@ -564,39 +614,60 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       // (a) S p, p^T S p, and the BF16 slices of p for the owned columns
       for (int f = tid; f < kNRMax; f += kBT) s_psp[f] = 0.0;
       __syncthreads();
+      // warp w takes RHS k = w, w + 8, ...; lane l the columns l + 32u of the
+      // tile, u = 0..3, with every load of the four issued before their use
       for (long long t = b; t < ntiles; t += G) {
-        for (int e = tid; e < NR * kTM; e += kBT) {
-          const int k = e / kTM;
-          const long long j = t * kTM + (e % kTM);
-          const long long o = (long long)k * p + j;
-          __nv_bfloat16 h = __float2bfloat16(0.f), m = h, l = h;
-          double v_psp = 0.0;
-          if (j < p && k < K && s_cga[k]) {
-            const double g = s_gam[k];
-            auto pv = [&](long long kk) -> double {
-              const long long ok = (long long)k * p + kk;
-              if (is_own(kk)) return pc[ok];
-              if (kcg == 0) return ldcg(pc + ok);
-              return fma(g, ldcg(po + ok), ldcg(P.z + ok));
-            };
-            const double pj = pc[o];
+        for (int k = warp; k < NR; k += kBT / 32) {
+          const bool act = k < K && s_cga[k];     // warp-uniform
+          const double g = act ? s_gam[k] : 0.0;
+          const long long ko = (long long)k * p;
+          auto pv = [&](long long kk) -> double {
+            if (is_own(kk)) return pc[ko + kk];
+            if (kcg == 0) return ldcg(pc + ko + kk);
+            return fma(g, ldcg(po + ko + kk), ldcg(P.z + ko + kk));
+          };
+          double pj[4], la[4], wl[4], wr[4], wu[4], wd[4], nl[4], nr[4], nu[4], nd[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const long long j = t * kTM + lane + 32 * u;
+            const bool ok = act && j < p;
+            const long long o = ko + j;
             const long long col = j % q2;
-            double lap = 0.0;
-            if (col != 0) lap = fma(P.wl[o], pj - pv(j - 1), lap);
-            if (col != q2 - 1 && j + 1 < p) lap = fma(P.wr[o], pj - pv(j + 1), lap);
-            if (j >= q2) lap = fma(P.wu[o], pj - pv(j - q2), lap);
-            if (j + q2 < p) lap = fma(P.wd[o], pj - pv(j + q2), lap);
-            const double spj = fma(P.la[o], pj, lap);
-            P.q[o] = spj;
-            v_psp = pj * spj;
-            split3(pj, h, m, l);
+            pj[u] = ok ? pc[o] : 0.0;
+            la[u] = ok ? P.la[o] : 0.0;
+            wl[u] = ok ? P.wl[o] : 0.0;
+            wr[u] = ok ? P.wr[o] : 0.0;
+            wu[u] = ok ? P.wu[o] : 0.0;
+            wd[u] = ok ? P.wd[o] : 0.0;
+            nl[u] = (ok && col != 0) ? pv(j - 1) : 0.0;
+            nr[u] = (ok && col != q2 - 1 && j + 1 < p) ? pv(j + 1) : 0.0;
+            nu[u] = (ok && j >= q2) ? pv(j - q2) : 0.0;
+            nd[u] = (ok && j + q2 < p) ? pv(j + q2) : 0.0;
           }
-          if (k < K) wadd(&s_psp[k], v_psp);       // k is warp-uniform
-          if (j < p) {
-            P.Ps[(0LL * NR + k) * P.ldp + j] = h;
-            P.Ps[(1LL * NR + k) * P.ldp + j] = m;
-            P.Ps[(2LL * NR + k) * P.ldp + j] = l;
+          double v_psp = 0.0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const long long j = t * kTM + lane + 32 * u;
+            __nv_bfloat16 h = __float2bfloat16(0.f), m = h, l = h;
+            if (act && j < p) {
+              const long long col = j % q2;
+              double lap = 0.0;
+              if (col != 0) lap = fma(wl[u], pj[u] - nl[u], lap);
+              if (col != q2 - 1 && j + 1 < p) lap = fma(wr[u], pj[u] - nr[u], lap);
+              if (j >= q2) lap = fma(wu[u], pj[u] - nu[u], lap);
+              if (j + q2 < p) lap = fma(wd[u], pj[u] - nd[u], lap);
+              const double spj = fma(la[u], pj[u], lap);
+              P.q[ko + j] = spj;
+              v_psp = fma(pj[u], spj, v_psp);
+              split3(pj[u], h, m, l);
+            }
+            if (j < p) {
+              P.Ps[(0LL * NR + k) * P.ldp + j] = h;
+              P.Ps[(1LL * NR + k) * P.ldp + j] = m;
+              P.Ps[(2LL * NR + k) * P.ldp + j] = l;
+            }
           }
+          if (k < K) wadd(&s_psp[k], v_psp);
         }
       }
       __syncthreads();
@@ -681,34 +752,55 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         if (!tc_tile(tp, P.Xt + t * kTM * P.ldn, P.ldn, rows, 0, P.ldn, P.Us, P.ldn,
                      (long long)NR * P.ldn, 0, P.ldn, P.ldn, NR)) { alive = false; break; }
         tmem_to_smem(tp.tmem, ts, NR);
-        for (int e = tid; e < K * kTM; e += kBT) {
-          const int k = e / kTM, cl = e % kTM;
-          const long long j = t * kTM + cl;
+        const bool jac = P.precond == PC_JACOBI;
+        for (int k = warp; k < K; k += kBT / 32) {   // as in (a): warp per RHS, 4 columns per lane
           if (!s_cga[k]) continue;                  // warp-uniform
+          const double nu = s_nu[k];
+          const long long ko = (long long)k * p;
+          double t0v[4], qv[4], pv4[4], xv[4], rv[4], iv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const long long j = t * kTM + lane + 32 * u;
+            const bool ok = j < p;
+            const long long o = ko + j;
+            t0v[u] = ok ? P.t0[o] : 0.0;
+            qv[u] = ok ? P.q[o] : 0.0;
+            pv4[u] = ok ? pc[o] : 0.0;
+            xv[u] = ok ? P.x[o] : 0.0;
+            rv[u] = ok ? P.r[o] : 0.0;
+            iv[u] = (ok && jac) ? P.idg[o] : 0.0;
+          }
           double v_rz = 0.0, v_rr = 0.0;
-          if (j < p) {
-            const long long o = (long long)k * p + j;
-            const double nu = s_nu[k];
-            const double tj = (double)ts[k * kTM + cl];
-            P.t0[o] = fma(nu, tj, P.t0[o]);           // tracked X^T X x
-            const double qj = tj + P.q[o];
-            P.x[o] = fma(nu, pc[o], P.x[o]);
-            const double rj = fma(-nu, qj, P.r[o]);
-            P.r[o] = rj;
-            v_rr = rj * rj;
-            if (P.precond == PC_JACOBI) {
-              const double zj = rj * P.idg[o];
-              P.z[o] = zj;
-              v_rz = rj * zj;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int cl = lane + 32 * u;
+            const long long j = t * kTM + cl;
+            if (j < p) {
+              const long long o = ko + j;
+              const double tj = (double)ts[k * kTM + cl];
+              P.t0[o] = fma(nu, tj, t0v[u]);            // tracked X^T X x
+              const double qj = tj + qv[u];
+              P.x[o] = fma(nu, pv4[u], xv[u]);
+              const double rj = fma(-nu, qj, rv[u]);
+              P.r[o] = rj;
+              v_rr = fma(rj, rj, v_rr);
+              if (jac) {
+                const double zj = rj * iv[u];
+                P.z[o] = zj;
+                v_rz = fma(rj, zj, v_rz);
+              }
             }
           }
-          if (P.precond == PC_JACOBI) wadd(&loc[k], v_rz);
+          if (jac) wadd(&loc[k], v_rz);
           wadd(&loc[kNRMax + k], v_rr);
         }
         __syncthreads();
         if (P.precond != PC_JACOBI) {
-          if (tid < K && s_cga[tid])
-            atomicAdd(&loc[tid], tile_solve(P, tid, t * kTM, rows, nullptr));
+          for (int k = tid >> 5; k < K; k += kBT / 32)   // one warp per RHS
+            if (s_cga[k]) {
+              const double rz = tile_solve_warp(P, k, t * kTM, rows, nullptr);
+              if ((tid & 31) == 0) atomicAdd(&loc[k], rz);
+            }
           __syncthreads();
         }
       }
@@ -727,12 +819,22 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       {
         double* pn = pcur ? P.pb0 : P.pb1;
         for (long long t = b; t < ntiles; t += G)
-          for (int e = tid; e < K * kTM; e += kBT) {
-            const int k = e / kTM;
-            const long long j = t * kTM + (e % kTM);
-            if (j >= p || !s_cga[k]) continue;
-            const long long o = (long long)k * p + j;
-            pn[o] = fma(s_gam[k], pc[o], P.z[o]);
+          for (int k = warp; k < K; k += kBT / 32) {
+            if (!s_cga[k]) continue;                // warp-uniform
+            const double g = s_gam[k];
+            const long long ko = (long long)k * p;
+            double pv4[4], zv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const long long j = t * kTM + lane + 32 * u;
+              pv4[u] = j < p ? pc[ko + j] : 0.0;
+              zv[u] = j < p ? P.z[ko + j] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const long long j = t * kTM + lane + 32 * u;
+              if (j < p) pn[ko + j] = fma(g, pv4[u], zv[u]);
+            }
           }
       }
       pcur ^= 1;
@@ -740,6 +842,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       __syncthreads();
     }
     if (!alive) break;
+    cg_since_exact += kcg;
     if (tid < K) {
       if (s_act[tid]) { s_fp[tid] = s_f[tid]; s_mm[tid] += 1; }
     }

@@ -127,14 +127,19 @@ flr_status run(const SolveParams& P0, const void* Xt, const double* y, long long
   SolveParams P = P0;
   P.cnorm = cn > 0.0 ? cn : 1.0;
   auto kern = mm_solve_kernel<TX, GK_STENCIL>;
-  // per-kernel attribute shared with concurrent callers: always the device maximum
-  int dev = 0, smem_max = 0;
+  // per-kernel attribute shared with concurrent callers: always the most the
+  // device allows next to the kernel's static shared memory
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
   if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, (const void*)kern) != cudaSuccess) {
     (void)cudaGetLastError();
     return FLR_ECUDA;
   }
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess) {
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;
+  if (smem > (size_t)dyn_max) return FLR_ENOTIMPL;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess) {
     (void)cudaGetLastError();
     return FLR_ECUDA;
   }
@@ -179,12 +184,13 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0)
     return FLR_EINVAL;
   int precond = o.precond;
-  if (precond == FLR_PC_AUTO) precond = E->kind == FLR_E_CHAIN ? FLR_PC_TRIDIAG : FLR_PC_TWOLEVEL;
+  if (precond == FLR_PC_AUTO) precond = FLR_PC_TWOLEVEL;
   if (precond != FLR_PC_JACOBI && precond != FLR_PC_TRIDIAG && precond != FLR_PC_PAPER &&
       precond != FLR_PC_TWOLEVEL)
     return FLR_EINVAL;
-  const bool tri = precond == FLR_PC_TRIDIAG || precond == FLR_PC_PAPER;
   const bool two = precond == FLR_PC_TWOLEVEL;
+  // the kernel's local tridiagonal solve: TRIDIAG, PAPER, and TWOLEVEL on a chain
+  const bool tri = precond == FLR_PC_TRIDIAG || precond == FLR_PC_PAPER || (two && E->kind == FLR_E_CHAIN);
 
   int dev = 0, sm_count = 0, smem_max = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { (void)cudaGetLastError(); return FLR_ECUDA; }

@@ -38,7 +38,8 @@
 // every connected group of such strong couplings leaves Q with a tiny
 // eigenvalue along the group's constant vector, which Jacobi does not see.
 // The preconditioner adds a coarse correction on exactly those directions:
-//   M^-1 r = D^-1 r + sum_c 1_c (1_c^T r) / q_c,      D = diag(Q),
+//   M^-1 r = D^-1 r + sum_c 1_c (1_c^T r) / q_c,
+// D = diag(Q), or on a chain the chunk-tridiagonal part of Q (TRIDIAG),
 //   q_c = sum_{j in c} (d_j + lam1 a_j) + sum of lam2 w_e over edges e
 //         leaving c,
 // i.e. the diagonal of P^T Q P for the piecewise-constant P of the groups,
@@ -340,11 +341,11 @@ __device__ __forceinline__ void setup_tridiag(const SolveParams& P, long long j0
 // shared memory and to global memory (neighbouring blocks read it as halo).
 // Jacobi: r / diag(Q).  Tridiagonal: parallel cyclic reduction with the
 // multipliers precomputed once per MM iteration (K1, K2, binv).
-__device__ __forceinline__ void apply_precond(const SolveParams& P, long long j0, int wl,
+__device__ __forceinline__ void apply_precond(const SolveParams& P, bool tri, long long j0, int wl,
                                               const double* sidg, const double* rsm,
                                               double* zsm, double* w0, double* w1) {
   const int tid = threadIdx.x;
-  if (P.precond == PC_JACOBI || P.precond == PC_TWOLEVEL) {
+  if (!tri) {
     for (int jj = tid; jj < wl; jj += kThreads) {
       const double z = rsm[jj] * sidg[jj];
       zsm[jj] = z;
@@ -540,6 +541,10 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   };
   const int rep = b % kUR;   // this block's accumulator replica
   const bool two = P.precond == PC_TWOLEVEL;
+  // local part of M: the chunk-tridiagonal solve (TRIDIAG, PAPER, and TWOLEVEL
+  // on a chain), else the diagonal
+  const bool tri = GK == GK_STENCIL &&
+                   (P.precond == PC_TRIDIAG || P.precond == PC_PAPER || (two && P.q2 >= P.p));
   const int lane = tid & 31, warp = tid >> 5;
 
   // ---- initialisation (Algorithm 1): beta_j = X_j^T y / X_j^T X_j
@@ -627,13 +632,12 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       const double dq = fma(P.lam2, deg, la + P.d[j]);
       s_idg[jj] = 1.0 / dq;
       qs[jj] = fma(la, xj, P.lam2 * lap);      // S x
-      tv[jj] = (P.precond == PC_TRIDIAG) ? dq : dq - P.d[j];   // tridiagonal diagonal
+      tv[jj] = (P.precond == PC_PAPER) ? dq - P.d[j] : dq;   // tridiagonal diagonal
       vsd[jj] = xj;
       xs[jj] = xj;
     }
     __syncthreads();
-    if ((P.precond == PC_TRIDIAG || P.precond == PC_PAPER) && GK == GK_STENCIL)
-      setup_tridiag(P, j0, wl, tv, s_wl, s_wr, pw);
+    if (tri) setup_tridiag(P, j0, wl, tv, s_wl, s_wr, pw);
     // ---------------- u0 = X x in FP64 (refinement pass)
     zero_u(U1);
     phase_a<TX, double>(P, Xt, j0, wl, vsd, redd, reinterpret_cast<double*>(U0) + (long long)rep * P.ldn);
@@ -739,7 +743,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       for (long long c = j0 + tid; c < j1 && c < nc; c += kThreads) P.qci[c] = 1.0 / ldcg(P.qc + c);
       __syncthreads();
     }
-    apply_precond(P, j0, wl, s_idg, rsm, zs, pw, pw + wp);
+    apply_precond(P, tri, j0, wl, s_idg, rsm, zs, pw, pw + wp);
     if (two) {   // z0 = D^-1 r0 + coarse part
       for (int jj = tid; jj < wl; jj += kThreads) {
         const int c = cid_s[jj];
@@ -841,7 +845,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
         rsm[jj] = fma(-nu, tv[jj] + qs[jj], rsm[jj]);
       }
       __syncthreads();
-      apply_precond(P, j0, wl, s_idg, rsm, zs, pw, pw + wp);
+      apply_precond(P, tri, j0, wl, s_idg, rsm, zs, pw, pw + wp);
       if (two) {
         // 1_c^T r into this iteration's accumulator; clear the previous one (its
         // readers, the p update and the halo of phase A, finished before barrier 1)
@@ -861,9 +865,16 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       if (!grid_sum(rzn)) return;
       if (two) {   // r^T z += sum_c (1_c^T r)^2 / q_c, in the same order in every block
         double cz[1] = {0.0};
-        for (int c = tid; c < nc; c += kThreads) {
-          const double sv_ = ldcg(Scur + c);
-          cz[0] = fma(sv_ * sv_, ldcg(P.qci + c), cz[0]);
+        for (int c0 = tid; c0 < nc; c0 += 4 * kThreads) {   // 8 loads in flight per thread
+          double sv_[4], qv_[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * kThreads;
+            sv_[u] = c < nc ? ldcg(Scur + c) : 0.0;
+            qv_[u] = c < nc ? ldcg(P.qci + c) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) cz[0] = fma(sv_[u] * sv_[u], qv_[u], cz[0]);
         }
         block_reduce<1>(cz, rs, kThreads);
         rzn[0] += cz[0];

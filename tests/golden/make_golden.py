@@ -35,6 +35,7 @@ def cases():
         "config2_q20": (lambda: fi.config(2, scale=0.04), "dense", None),
         "config2_q40": (lambda: fi.config(2, scale=0.16), "woodbury", None),
         "config4_small": (lambda: fi.config(4, scale=0.004), "dense", None),
+        "config4_q50x80": (lambda: fi.config(4, scale=0.04), "woodbury", None),
         "config3_small": (lambda: fi.config(3, scale=0.02), "dense", "grid"),
         "paper_c1_p200": (lambda: fi.paper_scenario(1, 200, eps=1e-6), "dense", None),
         "config2": (lambda: fi.config(2), "woodbury", None),

@@ -136,6 +136,42 @@ def test_config4_lattice_f16_small(flr):
     assert_parity(st, beta, g["f"], np.array(g["beta"]))
 
 
+def test_config4_q50x80_against_oracle(flr):
+    """The config-4 generator at 50x80 (p=4000, n=200, FP16 AR(1) rows) against the
+    stored Woodbury-oracle solve."""
+    g = golden("config4_q50x80")
+    pr = fi.config(4, scale=0.04)
+    check_fingerprint(pr, g)
+    prob = problem(flr, pr)
+    beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-12, tol_cg=1e-10, max_mm=20000)
+    assert_parity(st, beta, g["f"], np.array(g["beta"]))
+
+
+def test_config4_full_size_is_stationary(flr):
+    """Config 4 at full size (250x400 lattice, n=5000, FP16 X, 1 GB): too large for the
+    oracle's MM, so the property that holds at any size is checked instead.  The
+    MM limit is a stationary point of f_eps (Lemma 2): the oracle's gradient
+    X^T(X b - y) + lam1 A b + lam2 B b at the returned b is ~5e-7 ||X^T y|| for an
+    MM stopped at tol 1e-9 (measured on the 20x20 instance); a dropped term or a
+    wrong sign anywhere leaves it orders of magnitude larger.  The objective the
+    kernel reports must equal the oracle's f at the returned b."""
+    pr = fi.config(4)
+    prob = problem(flr, pr)
+    beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-9, tol_cg=1e-8, max_mm=20000)
+    assert st.status == 0, st
+    del prob
+    b = beta.cpu().numpy()
+    X = pr.X64()
+    E = pr.graph.edges
+    c = X.T @ pr.y
+    grad = mm.surrogate_gradient(X, pr.y, b, pr.lam1, pr.lam2, E, pr.eps)
+    ratio = np.linalg.norm(grad) / np.linalg.norm(c)
+    assert ratio <= 1e-5, (ratio, st)
+    f_host = mm.objective(X, pr.y, b, pr.lam1, pr.lam2, E)
+    assert abs(f_host - st.f) <= 1e-9 * abs(f_host), (f_host, st.f)
+    assert 0.0 <= f_host - mm.objective_eps(X, pr.y, b, pr.lam1, pr.lam2, E, pr.eps)
+
+
 def test_bf16_chain_against_inline_oracle(flr):
     pr = fi.config(3, scale=0.01)        # n=20, p=200, BF16 X
     lam1, lam2 = 0.1, 0.3
