@@ -20,10 +20,17 @@ enum DevErr : int { DERR_NONE = 0, DERR_TIMEOUT = 1 };
 // ---------------------------------------------------------------------------
 template <typename TX> struct XT;
 
+// X is re-read every CG iteration: its loads skip L1 and carry an L2
+// evict_last policy, so other traffic (an L2 flush, the vectors) evicts X last.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
 __device__ __forceinline__ uint4 ld_stream16(const void* p) {
   uint4 r;
-  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p), "l"(l2_keep_policy()));
   return r;
 }
 
