@@ -77,3 +77,70 @@ def test_footprint_estimate_is_monotone_and_validates(lib):
     assert f(1000, 20000, 19800, 1, 0) > base
     assert f(1000, 10000, 19800, 2, 0) < base  # 16-bit X
     assert f(0, 10, 9, 1, 0) < 0 and f(10, 10, 9, 7, 0) < 0
+
+
+def _c_layout():
+    """sizeof/offsetof of the header's structs and its enum values, from a C program
+    compiled against include/flr.h (gcc; no CUDA needed)."""
+    import shutil
+    import subprocess
+    import tempfile
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    fields = {
+        "flr_graph": ["kind", "q1", "q2", "edges", "m"],
+        "flr_opts": ["max_mm", "max_cg", "min_cg", "precond", "tol_cg", "grid", "inject_stall",
+                     "wait_cycles", "refine_every"],
+        "flr_stats": [],
+        "flr_server_opts": [],
+        "flr_request": [],
+        "flr_result": [],
+    }
+    enums = ["FLR_OK", "FLR_EINVAL", "FLR_ENOMEM", "FLR_ECUDA", "FLR_ENOTCONV", "FLR_EBREAKDOWN",
+             "FLR_ENONFINITE", "FLR_ETIMEOUT", "FLR_ENOTIMPL", "FLR_ESCRATCH", "FLR_F64", "FLR_F32",
+             "FLR_BF16", "FLR_F16", "FLR_MEM_DEVICE", "FLR_MEM_HOST", "FLR_E_CHAIN", "FLR_E_LATTICE",
+             "FLR_E_EDGES", "FLR_PC_AUTO", "FLR_PC_JACOBI", "FLR_PC_TRIDIAG", "FLR_PC_PAPER",
+             "FLR_PC_TWOLEVEL"]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "flr.h"', "int main(void) {"]
+    for st, fs in fields.items():
+        lines.append(f'  printf("size {st} %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'  printf("off {st}.{f} %zu\\n", offsetof({st}, {f}));')
+    for e in enums:
+        lines.append(f'  printf("enum {e} %d\\n", (int){e});')
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        with open(src, "w") as fh:
+            fh.write("\n".join(lines))
+        subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), src, "-o", exe],
+                       check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    res = {}
+    for ln in out.splitlines():
+        kind, key, val = ln.split()
+        res[(kind, key)] = int(val)
+    return res
+
+
+def test_binding_structs_and_enums_match_the_header():
+    """The ctypes mirrors in the binding have the header's sizes, field offsets
+    and enum values, so no call marshals a shifted field."""
+    import paper_1306_1970_gb300 as flr
+    c = _c_layout()
+    mirrors = {"flr_graph": flr.FlrGraph, "flr_opts": flr.FlrOpts, "flr_stats": flr.FlrStats,
+               "flr_server_opts": flr.FlrServerOpts, "flr_request": flr.FlrRequest,
+               "flr_result": flr.FlrResult}
+    for name, cls in mirrors.items():
+        assert ctypes.sizeof(cls) == c[("size", name)], name
+    for (kind, key), val in c.items():
+        if kind == "off":
+            st, f = key.split(".")
+            assert getattr(mirrors[st], f).offset == val, key
+    for (kind, key), val in c.items():
+        if kind != "enum":
+            continue
+        if key.startswith("FLR_PC_"):
+            assert flr.PRECOND[key[len("FLR_PC_"):].lower()] == val, key
+        else:
+            assert getattr(flr, key) == val, key
