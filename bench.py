@@ -17,6 +17,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -40,7 +41,7 @@ def parse():
     ap.add_argument("--precond", default="auto")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--requests", type=int, default=120, help="served stream length (serve5)")
+    ap.add_argument("--requests", type=int, default=24, help="served stream length (serve5)")
     ap.add_argument("--served-slots", type=int, default=4,
                     help="concurrent copies for the served-form measurement (0 = skip)")
     ap.add_argument("--slots", type=int, default=4)
@@ -120,8 +121,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                                 else "_work", f"clocks_{os.getpid()}.csv")
+        # raw samples go to FLR_CLOCKS_DIR (default: the system temp directory)
+        self.path = os.path.join(os.environ.get("FLR_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"flr_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"

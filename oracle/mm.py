@@ -20,7 +20,7 @@ using majorization-minimization and parallel processing".
                    with a banded/sparse factor of lam1 A + lam2 B (same
                    iterates as mm_dense up to rounding; for large p)
 
-Readings where the paper is silent (listed in the design doc as well):
+Readings where the paper is silent:
   * a zero column (X_j^T X_j = 0) initialises beta_j = 0;
   * the outer stop uses the true objective f (Algorithm 1, RE in Section 5);
   * the "dpotri" inverse of Algorithm 1 is read as a Cholesky solve with

@@ -55,6 +55,9 @@ def solve(pr, solver, lam1, lam2, log=None):
     out = {"lam1": lam1, "lam2": lam2, "f": r.f, "f_eps": r.f_eps, "iters": r.iters,
            "rel_change": r.rel_change, "seconds": time.time() - t,
            "f_trace_head": [float(v) for v in r.f_trace[:3]]}
+    # first MM iteration whose objective is within 1e-6 of the converged one
+    gaps = np.abs(np.asarray(r.f_trace) - r.f) / abs(r.f)
+    out["iters_to_gap_1e-6"] = int(np.argmax(gaps <= 1e-6))
     b = r.beta
     out["beta_absmax"] = float(np.abs(b).max())
     if b.shape[0] <= 4096:
