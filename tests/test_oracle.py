@@ -274,3 +274,34 @@ def test_mm_iteration_counts_match_table_c1(g, row):
     r = mm.mm_woodbury(pr.X64(), pr.y, pr.graph.edges, row["lam1"], row["lam2"], g["eps"],
                        tol=g["tol"])
     assert abs(r.iters - row["mm_iters"]) <= 0.2 * row["mm_iters"] + 0.5, (r.iters, row)
+
+
+def test_knn_graph_is_a_symmetric_set_containing_each_points_neighbours():
+    """5-NN edges: pairs j < k, no duplicates or self loops, and every point is joined
+    to its 5 nearest (by brute force; ties to the lower index)."""
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(size=(60, 2))
+    E = fi.knn_edges(pts, 5)
+    assert E.shape[1] == 2 and np.all(E[:, 0] < E[:, 1])
+    assert len({(int(a), int(b)) for a, b in E}) == E.shape[0]
+    S = {(int(a), int(b)) for a, b in E}
+    for j in range(pts.shape[0]):
+        d = np.linalg.norm(pts - pts[j], axis=1)
+        d[j] = np.inf
+        for k in np.argsort(d, kind="stable")[:5]:
+            assert (min(j, k), max(j, k)) in S
+
+
+def test_served_stream_follows_its_recipe():
+    """Served requests: p in range (lattices rounded to q1 x q2), n = p // 4, lambdas in
+    [1e-3, 1], both dtypes and all three graph kinds present, arrivals increasing."""
+    reqs = fi.served_stream(300, seed=11, p_lo=500, p_hi=50000)
+    assert all(b.arrival > a.arrival for a, b in zip(reqs, reqs[1:]))
+    for r in reqs:
+        assert 1e-3 <= r.lam1 <= 1.0 and 1e-3 <= r.lam2 <= 1.0
+        assert r.n == r.p // 4
+        if r.kind == "lattice":
+            assert r.q1 * r.q2 == r.p
+        assert 400 <= r.p <= 51000
+    assert {r.kind for r in reqs} == {"chain", "lattice", "knn"}
+    assert {r.dtype for r in reqs} == {"f32", "bf16"}
