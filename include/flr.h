@@ -175,7 +175,11 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
 /* Solve K independent (lambda1[k], lambda2[k]) problems on the same X, y, E
  * (a lambda grid).  betas is p x K column-major (column k = beta for pair k)
  * in `io_mem` memory; objectives (K doubles) and stats (K entries) are host
- * memory and optional.  Returns the first non-OK status over k, else FLR_OK. */
+ * memory and optional.  Returns the first non-OK status over k, else FLR_OK.
+ * BF16 X on a chain or lattice with precond AUTO, JACOBI, TRIDIAG or PAPER
+ * runs one tensor-core launch per 64 pairs (AUTO: the per-tile tridiagonal
+ * preconditioner); any other case solves the pairs one after another with
+ * flr_solve. */
 flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const double* lambda2,
                            double eps, double tol, const flr_opts* opts, double* betas,
                            int32_t io_mem, double* objectives, flr_stats* stats);

@@ -677,7 +677,7 @@ flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const doub
   flr_opts o;
   flr_default_opts(&o);
   if (opts) o = *opts;
-  // tensor-core multi-RHS path: BF16 X, chain/lattice, Jacobi preconditioner
+  // tensor-core multi-RHS path: BF16 X, chain/lattice, a diagonal or per-tile tridiagonal preconditioner
   const bool tc_path = h->dtype == FLR_BF16 && h->gkind != FLR_E_EDGES && K >= 1 &&
                        (o.precond == FLR_PC_AUTO || o.precond == FLR_PC_JACOBI ||
                         o.precond == FLR_PC_TRIDIAG || o.precond == FLR_PC_PAPER);
