@@ -112,11 +112,15 @@ typedef struct flr_opts {
                             the other blocks' bounded waits expire and the solve returns
                             FLR_ETIMEOUT (needs grid >= 2).  0 in normal use. */
     int64_t wait_cycles; /* bound of every device-side wait in SM clock cycles (0 = 2^33) */
-    int32_t refine_every;/* flr_solve_batch: X b and X^T X b are recomputed exactly in FP64 every
-                            this many MM iterations, after every 128 CG iterations, and
-                            before any problem is declared converged; in between they are
-                            advanced from the CG products (0 or 1 = every MM iteration, the
-                            default).  flr_solve always recomputes. */
+    int32_t max_refine;  /* refinement restarts of the inner solve per MM iteration (default 0).
+                            Every MM iteration starts CG from the residual c - Q x computed in
+                            FP64.  With max_refine = R > 0, once CG meets tol_cg on its
+                            recursive residual, the true residual of the same surrogate
+                            system is recomputed in FP64 and CG restarts from it, at most R
+                            times, until the true residual meets tol_cg too.  This solves
+                            each surrogate to FP64 accuracy from FP32/BF16/FP16 products, so
+                            the iterates follow the MM map of Algorithm 1 (mixed-precision
+                            iterative refinement).  flr_solve and flr_solve_noalloc only. */
     int32_t reserved[3];
 } flr_opts;
 
@@ -125,11 +129,20 @@ typedef struct flr_stats {
     int32_t cg_iters;        /* CG iterations summed over all MM iterations */
     int32_t status;          /* flr_status of the solve */
     int32_t grid;            /* thread blocks used */
-    double f;                /* f(beta) at the returned beta (Eq. obj) */
+    double f;                /* f(beta) at the returned beta (Eq. obj); the objective */
     double f_eps;            /* f_eps(beta) (Eq. pert) */
     double rel_change;       /* last |f(b_new) - f(b_old)| / |f(b_old)| */
-    double cg_relres;        /* ||r|| / ||X^T y|| at the end of the last inner solve */
+    double cg_relres;        /* ||r|| / ||X^T y|| at the end of the last inner solve (the
+                                FP64 true residual when the solve ended on a refinement) */
     double ms;               /* device time of the solve kernel, milliseconds */
+    int32_t refine_steps;    /* FP64 refinement passes inside MM iterations (opts.max_refine) */
+    int32_t reserved;
+    double est_err;          /* estimated relative error of f against the exact minimum f* of
+                                Eq. obj:  (f - f_eps)/f, the bound of Prop. 1(ii) on what the
+                                perturbation costs, plus the MM tail rel_change * q / (1 - q)
+                                with q = rel_change / (the change before it) capped at 0.999
+                                (a linear-convergence estimate; rel_change alone when fewer
+                                than two changes exist).  An estimate, not a bound. */
 } flr_stats;
 
 typedef struct flr_handle flr_handle;
@@ -224,10 +237,16 @@ flr_status flr_get_info(flr_t h, int64_t* n, int64_t* p, int64_t* m, int32_t* dt
  *   beta_out  p doubles, device memory.
  *   stream    cudaStream_t all work is issued on; the call returns when done.
  *   stats     optional, host memory (ms is host wall time).
- * Scratch needed (bytes, each part rounded up to 256): 256 + 32768 + 256
- * + 9*8*p + 2*8*ldn, plus 2*8*p*ceil(log2(ceil(p/grid))) for the tridiagonal
- * preconditioners.  A problem that needs more than FLR_NOALLOC_SCRATCH_BYTES
- * returns FLR_ESCRATCH before any GPU work.  Other errors as flr_solve. */
+ * Scratch needed, in bytes, with every term rounded up to a multiple of 256:
+ *     256 + 32768 + 256 + 7 * (8*p) + 2 * (8*ldn)
+ *   + 8 * (8*p)        with FLR_PC_TWOLEVEL (what FLR_PC_AUTO selects)
+ *   + 2 * (8*p*L)      with the chunk-tridiagonal solve (FLR_PC_TRIDIAG,
+ *                      FLR_PC_PAPER, and FLR_PC_TWOLEVEL on a chain),
+ * where L = ceil(log2(ceil(p / grid))) and grid is the block count of the
+ * launch (at most the number of SMs).  So the default on a chain takes
+ * about (15 + 2L) * 8 * p bytes.  A problem that needs more than
+ * FLR_NOALLOC_SCRATCH_BYTES returns FLR_ESCRATCH before any GPU work.
+ * Other errors as flr_solve. */
 flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n, int64_t p, int64_t ldn,
                              const double* y, const flr_graph* E, double lambda1, double lambda2,
                              double eps, double tol, const flr_opts* opts, double* beta_out,
@@ -278,6 +297,8 @@ typedef struct flr_result {
     flr_stats stats;
     double t_submit, t_start, t_end;   /* seconds since the server was created */
     int64_t footprint;      /* device bytes reserved for the request */
+    uint64_t dev_t0_ns, dev_t1_ns;     /* the GPU's global timer (ns) when the solve kernel
+                                          started and finished; comparable between requests */
 } flr_result;
 
 /* Start a server on the current device (opts may be NULL). */

@@ -42,14 +42,16 @@ class FlrOpts(ctypes.Structure):
     _fields_ = [("max_mm", ctypes.c_int32), ("max_cg", ctypes.c_int32), ("min_cg", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("tol_cg", ctypes.c_double), ("grid", ctypes.c_int32),
                 ("inject_stall", ctypes.c_int32), ("wait_cycles", ctypes.c_int64),
-                ("refine_every", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("max_refine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class FlrStats(ctypes.Structure):
     _fields_ = [("mm_iters", ctypes.c_int32), ("cg_iters", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("grid", ctypes.c_int32), ("f", ctypes.c_double),
                 ("f_eps", ctypes.c_double), ("rel_change", ctypes.c_double),
-                ("cg_relres", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("cg_relres", ctypes.c_double), ("ms", ctypes.c_double),
+                ("refine_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("est_err", ctypes.c_double)]
 
 
 class FlrServerOpts(ctypes.Structure):
@@ -68,7 +70,8 @@ class FlrRequest(ctypes.Structure):
 class FlrResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32), ("stats", FlrStats),
                 ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
-                ("t_end", ctypes.c_double), ("footprint", ctypes.c_int64)]
+                ("t_end", ctypes.c_double), ("footprint", ctypes.c_int64),
+                ("dev_t0_ns", ctypes.c_uint64), ("dev_t1_ns", ctypes.c_uint64)]
 
 
 class FlrError(RuntimeError):
@@ -164,11 +167,13 @@ class Stats:
     rel_change: float
     cg_relres: float
     ms: float
+    refine_steps: int = 0
+    est_err: float = float("nan")
 
     @classmethod
     def from_c(cls, s: FlrStats) -> "Stats":
         return cls(s.mm_iters, s.cg_iters, s.status, s.grid, s.f, s.f_eps, s.rel_change,
-                   s.cg_relres, s.ms)
+                   s.cg_relres, s.ms, s.refine_steps, s.est_err)
 
 
 def _torch():

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/flr.h"
+#include "flr_internal.h"
 #include "flr_solve.cuh"
 #include "flr_batch.cuh"
 
@@ -103,6 +104,7 @@ struct flr_handle {
   void* ub1 = nullptr;
   unsigned char* ctl = nullptr;     // barrier counter, error flag, DevStats
   unsigned char hctl[256];          // host copy of ctl (read once per solve)
+  unsigned long long span_t0 = 0, span_t1 = 0;   // global timer span of the last solve kernel
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<void*> allocs;
   // batched tensor-core path (allocated on first use)
@@ -114,7 +116,6 @@ struct flr_handle {
   double* bvec[15] = {nullptr};
   __nv_bfloat16 *Ps = nullptr, *Us = nullptr;
   float* Upart = nullptr;
-  float* Uf = nullptr;
   double *U0part = nullptr, *U0 = nullptr, *bred = nullptr, *blam = nullptr;
   unsigned char* bctl = nullptr;
   BatchStats* bstats = nullptr;
@@ -123,6 +124,22 @@ struct flr_handle {
 namespace {
 
 constexpr int kMaxGrid = 512;       // grid reductions use one thread per block
+
+// Makes `dev` current for the lifetime of the guard and restores the caller's
+// device on every return path.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev && cudaSetDevice(dev) == cudaSuccess) prev = cur;
+    (void)cudaGetLastError();
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
 
 flr_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return FLR_OK;
@@ -153,16 +170,15 @@ flr_status dalloc(flr_handle* h, T** out, size_t count) {
 
 void release(flr_handle* h) {
   if (!h) return;
-  int prev = 0;
-  cudaGetDevice(&prev);
-  cudaSetDevice(h->device);
-  if (h->stream) cudaStreamSynchronize(h->stream);
-  for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
-  h->allocs.clear();
-  if (h->stream) cudaStreamSynchronize(h->stream);
-  if (h->ev0) cudaEventDestroy(h->ev0);
-  if (h->ev1) cudaEventDestroy(h->ev1);
-  cudaSetDevice(prev);
+  {
+    DeviceGuard dg(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
+    h->allocs.clear();
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+  }
   delete h;
 }
 
@@ -281,7 +297,6 @@ flr_status batch_prepare(flr_handle* h) {
   if ((s = dalloc(h, &h->Us, (size_t)kSlices * kNRMax * h->ldn)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->Upart, (size_t)S * kNRMax * n)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->U0part, (size_t)S * kNRMax * n)) != FLR_OK) return s;
-  if ((s = dalloc(h, &h->Uf, (size_t)kNRMax * n)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->U0, (size_t)kNRMax * n)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->bred, (size_t)kRedSlots * 4 * kNRMax)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->blam, (size_t)2 * kNRMax)) != FLR_OK) return s;
@@ -336,8 +351,6 @@ flr_status batch_group(flr_handle* h, int K, const double* l1, const double* l2,
     P.precond = pc == FLR_PC_TRIDIAG ? PC_TRIDIAG : pc == FLR_PC_PAPER ? PC_PAPER : PC_JACOBI;
   }
   P.Ps = h->Ps; P.Us = h->Us; P.Upart = h->Upart; P.U0part = h->U0part; P.U0 = h->U0;
-  P.Uf = h->Uf;
-  P.refine_every = o.refine_every > 0 ? o.refine_every : 1;
   P.red = h->bred;
   P.bar = reinterpret_cast<unsigned*>(h->bctl);
   P.err = reinterpret_cast<int*>(h->bctl + 64);
@@ -401,6 +414,14 @@ flr_status batch_group(flr_handle* h, int K, const double* l1, const double* l2,
       stats[k].rel_change = hs[k].rel_change;
       stats[k].cg_relres = hs[k].cg_relres;
       stats[k].ms = ms;
+      stats[k].refine_steps = 0;
+      stats[k].reserved = 0;
+      DevStats ds{};
+      ds.f = hs[k].f;
+      ds.f_eps = stats[k].f_eps;
+      ds.rel_change = hs[k].rel_change;
+      ds.rel_prev = hs[k].rel_prev;
+      stats[k].est_err = estimated_error(ds);
     }
     if (sk != FLR_OK && first == FLR_OK) first = sk;
   }
@@ -569,11 +590,9 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   flr_default_opts(&o);
   if (opts) o = *opts;
   if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0 ||
-      o.refine_every < 0)
+      o.max_refine < 0)
     return FLR_EINVAL;
-  int prev_dev = 0;
-  cudaGetDevice(&prev_dev);
-  if (prev_dev != h->device) cudaSetDevice(h->device);
+  DeviceGuard dg(h->device);
 
   int precond = o.precond;
   if (precond == FLR_PC_AUTO) precond = FLR_PC_TWOLEVEL;
@@ -623,6 +642,7 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   P.lam1 = lambda1; P.lam2 = lambda2; P.eps = eps; P.tol = tol;
   P.tol_cg = o.tol_cg > 0.0 ? o.tol_cg : tol;
   P.max_mm = o.max_mm; P.max_cg = o.max_cg; P.min_cg = o.min_cg; P.precond = precond;
+  P.max_refine = o.max_refine;
   P.w = w; P.wpad = wpad; P.levels = levels;
   P.beta_init = binit;
   P.x = h->x; P.z = h->z; P.pb0 = h->pb0; P.pb1 = h->pb1; P.wc = h->wc;
@@ -660,8 +680,12 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
     stats->rel_change = hs->rel_change;
     stats->cg_relres = hs->cg_relres;
     stats->ms = ms;
+    stats->refine_steps = hs->refine_steps;
+    stats->reserved = 0;
+    stats->est_err = estimated_error(*hs);
   }
-  if (prev_dev != h->device) cudaSetDevice(prev_dev);
+  h->span_t0 = hs->t0_ns;
+  h->span_t1 = hs->t1_ns;
   return st;
 }
 
@@ -677,6 +701,10 @@ flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const doub
   flr_opts o;
   flr_default_opts(&o);
   if (opts) o = *opts;
+  if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0 ||
+      o.max_refine < 0)
+    return FLR_EINVAL;
+  DeviceGuard dg(h->device);
   // tensor-core multi-RHS path: BF16 X, chain/lattice, a diagonal or per-tile tridiagonal preconditioner
   const bool tc_path = h->dtype == FLR_BF16 && h->gkind != FLR_E_EDGES && K >= 1 &&
                        (o.precond == FLR_PC_AUTO || o.precond == FLR_PC_JACOBI ||
@@ -707,6 +735,15 @@ flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const doub
 }
 
 void flr_destroy(flr_t h) { release(h); }
+
+}  // extern "C"
+
+void flr_kernel_span(flr_t h, unsigned long long* t0, unsigned long long* t1) {
+  *t0 = h ? h->span_t0 : 0;
+  *t1 = h ? h->span_t1 : 0;
+}
+
+extern "C" {
 
 flr_status flr_get_info(flr_t h, int64_t* n, int64_t* p, int64_t* m, int32_t* dtype) {
   if (!h) return FLR_EINVAL;

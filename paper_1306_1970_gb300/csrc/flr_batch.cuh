@@ -31,14 +31,11 @@ constexpr int kTM = 128;                 // tile rows (MMA M); the element loops
 constexpr int kNS = 3;                   // cp.async / MMA pipeline stages
 constexpr int kSlices = 3;               // BF16 slices per FP64/FP32 operand
 constexpr int kRedSlots = 3;
-// Tracked X b and X^T X b drift with every CG step (FP32-level products), so
-// an exact FP64 pass is also forced once this many lockstep CG iterations
-// have run since the last one.
-constexpr int kTrackMaxCG = 128;
 
 struct BatchStats {
   int mm_iters, cg_iters, status, pad;
   double f, f_eps, rel_change, cg_relres;
+  double rel_prev;             // the relative change of f one MM iteration earlier
 };
 
 struct BatchParams {
@@ -55,7 +52,6 @@ struct BatchParams {
   double eps, tol, tol_cg;
   int max_mm, max_cg, min_cg;
   int precond;                 // PC_JACOBI, PC_TRIDIAG or PC_PAPER
-  int refine_every;            // exact FP64 X b / X^T X b every this many MM iterations
   int S;                       // split-K chunks per row tile in phase A
   long long kchunk;            // columns per split-K chunk (multiple of 64)
   // per-RHS FP64 state, layout [k][j]
@@ -64,7 +60,6 @@ struct BatchParams {
   __nv_bfloat16* Ps;           // [3][NR][ldp]
   __nv_bfloat16* Us;           // [3][NR][ldn]
   float* Upart;                // [S][NR][n]
-  float* Uf;                   // [NR][n]  U = X p of the current CG iteration
   double* U0part;              // [S][NR][n]
   double* U0;                  // [NR][n]
   double* red;                 // [kRedSlots][4*kNRMax]
@@ -309,7 +304,8 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
   double* s_rel = scal + 6 * kNRMax;   double* s_rss = scal + 7 * kNRMax;
   double* s_relres = scal + 8 * kNRMax; double* s_pen = scal + 9 * kNRMax;   // 2 * kNRMax
   double* s_psp = scal + 11 * kNRMax;  double* s_uu = scal + 12 * kNRMax;
-  int* s_act = reinterpret_cast<int*>(scal + 13 * kNRMax);      // MM-active
+  double* s_relp = scal + 13 * kNRMax;
+  int* s_act = reinterpret_cast<int*>(scal + 14 * kNRMax);      // MM-active
   int* s_cga = s_act + kNRMax;                                     // CG-active
   int* s_mm = s_act + 2 * kNRMax;
   int* s_cg = s_act + 3 * kNRMax;
@@ -354,11 +350,10 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
     }
   for (int k = tid; k < kNRMax; k += kBT) {
     s_act[k] = k < K ? 1 : 0; s_cga[k] = 0; s_mm[k] = 0; s_cg[k] = 0; s_st[k] = 0;
-    s_f[k] = 0.0; s_fp[k] = 0.0; s_rel[k] = 0.0; s_relres[k] = 0.0;
+    s_f[k] = 0.0; s_fp[k] = 0.0; s_rel[k] = 0.0; s_relres[k] = 0.0; s_relp[k] = 0.0;
   }
   bool alive = gb.sync();
   int mm = 0, pcur = 0;
-  long long cg_since_exact = 0;   // lockstep CG iterations since the last exact pass
   auto is_own = [&](long long j) -> bool { return ((j / kTM) % G) == b; };
   // In the tile loops below all 32 lanes of a warp share one RHS index k
   // (128 columns per k, a multiple of 32), so per-RHS sums reduce by warp
@@ -409,55 +404,46 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
           tile_factor(P, tid, t * kTM, (int)(p - t * kTM < kTM ? p - t * kTM : kTM));
     }
     // ---------------- objective and outer stop.  u0 = X b and X^T X b are
-    // recomputed exactly in FP64 every refine_every MM iterations and whenever
-    // a right-hand side would otherwise stop; in between they are advanced from
-    // the CG iterations' own products (FP64 accumulation of FP32-accurate terms).
-    bool exact = (mm % P.refine_every) == 0 || cg_since_exact >= kTrackMaxCG;
-    bool pen_done = false;
-    while (true) {
-      if (exact) {
-        // FP64 refinement pass 1: U0 = X b (CUDA cores, FP64)
-        for (long long it = b; it < mtiles * P.S; it += G) {
-          const long long mt = it % mtiles, sp = it / mtiles;
-          const long long jb = sp * P.kchunk, je = jb + P.kchunk < p ? jb + P.kchunk : p;
-          const int row = tid % kTM, h = tid / kTM;       // 2 halves of 32 RHS
-          const long long i = mt * kTM + row;
-          double acc[32];
-          #pragma unroll
-          for (int m = 0; m < 32; ++m) acc[m] = 0.0;
-          for (long long j0 = jb; j0 < je; j0 += 64) {
-            __syncthreads();
-            for (int e = tid; e < 64 * kNRMax; e += kBT) {
-              const int jj = e / kNRMax, k = e % kNRMax;
-              const long long j = j0 + jj;
-              b64[jj * kNRMax + k] = (k < K && s_act[k] && j < je) ? ldcg(P.x + (long long)k * p + j) : 0.0;
-            }
-            __syncthreads();
-            const int jn = (int)(je - j0 < 64 ? je - j0 : 64);
-            if (i < n) {
-              for (int jj = 0; jj < jn; ++jj) {
-                const double xv = (double)__bfloat162float(P.Xt[(j0 + jj) * P.ldn + i]);
-                const double* bb = b64 + jj * kNRMax + h * 32;
-                #pragma unroll
-                for (int m = 0; m < 32; ++m) acc[m] = fma(xv, bb[m], acc[m]);
-              }
+    // recomputed exactly in FP64 on the CUDA cores every MM iteration.
+    {
+      // FP64 refinement pass 1: U0 = X b (CUDA cores, FP64)
+      for (long long it = b; it < mtiles * P.S; it += G) {
+        const long long mt = it % mtiles, sp = it / mtiles;
+        const long long jb = sp * P.kchunk, je = jb + P.kchunk < p ? jb + P.kchunk : p;
+        const int row = tid % kTM, h = tid / kTM;       // 2 halves of 32 RHS
+        const long long i = mt * kTM + row;
+        double acc[32];
+        #pragma unroll
+        for (int m = 0; m < 32; ++m) acc[m] = 0.0;
+        for (long long j0 = jb; j0 < je; j0 += 64) {
+          __syncthreads();
+          for (int e = tid; e < 64 * kNRMax; e += kBT) {
+            const int jj = e / kNRMax, k = e % kNRMax;
+            const long long j = j0 + jj;
+            b64[jj * kNRMax + k] = (k < K && s_act[k] && j < je) ? ldcg(P.x + (long long)k * p + j) : 0.0;
+          }
+          __syncthreads();
+          const int jn = (int)(je - j0 < 64 ? je - j0 : 64);
+          if (i < n) {
+            for (int jj = 0; jj < jn; ++jj) {
+              const double xv = (double)__bfloat162float(P.Xt[(j0 + jj) * P.ldn + i]);
+              const double* bb = b64 + jj * kNRMax + h * 32;
+              #pragma unroll
+              for (int m = 0; m < 32; ++m) acc[m] = fma(xv, bb[m], acc[m]);
             }
           }
-          if (i < n) {
-            #pragma unroll
-            for (int m = 0; m < 32; ++m) {
-              const int k = h * 32 + m;
-              if (k < NR) P.U0part[((long long)sp * NR + k) * n + i] = acc[m];
-            }
+        }
+        if (i < n) {
+          #pragma unroll
+          for (int m = 0; m < 32; ++m) {
+            const int k = h * 32 + m;
+            if (k < NR) P.U0part[((long long)sp * NR + k) * n + i] = acc[m];
           }
         }
       }
       __syncthreads();
-      if (!pen_done) {
-        if (!grid_red(s_pen, s_pen, 2 * kNRMax)) { alive = false; break; }
-        pen_done = true;
-      } else if (!gb.sync()) { alive = false; break; }
-      // U0 (exact: sum of the split partials) and the residual sum of squares
+      if (!grid_red(s_pen, s_pen, 2 * kNRMax)) { alive = false; break; }
+      // U0 = sum of the split partials, and the residual sum of squares
       for (int f = tid; f < kNRMax; f += kBT) s_rss[f] = 0.0;
       __syncthreads();
       {
@@ -467,34 +453,16 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
           const int k = (int)(e / (i1 - i0));
           const long long i = i0 + e % (i1 - i0);
           if (!s_act[k]) continue;
-          double sv;
-          if (exact) {
-            sv = 0.0;
-            for (int sp = 0; sp < P.S; ++sp) sv += ldcg(P.U0part + ((long long)sp * NR + k) * n + i);
-            P.U0[(long long)k * n + i] = sv;
-          } else {
-            sv = P.U0[(long long)k * n + i];
-          }
+          double sv = 0.0;
+          for (int sp = 0; sp < P.S; ++sp) sv += ldcg(P.U0part + ((long long)sp * NR + k) * n + i);
+          P.U0[(long long)k * n + i] = sv;
           const double rr = P.y[i] - sv;
           atomicAdd(&s_rss[k], rr * rr);
         }
       }
       __syncthreads();
       if (!grid_red(s_rss, s_rss, kNRMax)) { alive = false; break; }
-      // f(beta_k) (Eq. obj); a tracked value that passes the stop test is re-checked exactly
-      if (tid == 0) s_rz[0] = 0.0;
-      __syncthreads();
-      if (tid < K && s_act[tid]) {
-        const int k = tid;
-        const double fk = 0.5 * s_rss[k] + P.lam1[k] * s_pen[k] + P.lam2[k] * s_pen[kNRMax + k];
-        if (!exact && s_mm[k] > 0 && fabs(fk - s_fp[k]) <= P.tol * fabs(s_fp[k])) s_rz[0] = 1.0;
-      }
-      __syncthreads();
-      if (!exact && s_rz[0] != 0.0) { exact = true; __syncthreads(); continue; }
-      break;
     }
-    if (exact) cg_since_exact = 0;
-    if (!alive) break;
     if (tid < K) {
       const int k = tid;
       if (s_act[k]) {
@@ -502,6 +470,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         s_f[k] = fk;
         if (!isfinite(fk)) { s_act[k] = 0; s_st[k] = ST_NONFINITE; }
         else if (s_mm[k] > 0) {
+          s_relp[k] = s_rel[k];
           s_rel[k] = fabs(fk - s_fp[k]) / fabs(s_fp[k]);
           if (s_rel[k] <= P.tol) s_act[k] = 0;
         }
@@ -515,7 +484,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
     // ---------------- FP64 refinement pass 2: r0 = c - X^T U0 - S b; z0; p1 = z0
     for (int f = tid; f < kNRMax; f += kBT) { s_rz[f] = 0.0; s_rr[f] = 0.0; }
     __syncthreads();
-    for (long long t = b; exact && t < ntiles; t += G) {
+    for (long long t = b; t < ntiles; t += G) {
       const int cl = tid % kTM, h = tid / kTM;
       const long long j = t * kTM + cl;
       double acc[32];
@@ -707,7 +676,6 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
             for (int sp = 0; sp < P.S; ++sp) s += (double)ldcg(P.Upart + ((long long)sp * NR + k) * n + i);
           __nv_bfloat16 h, m, l;
           split3(s, h, m, l);
-          if (i < n) P.Uf[(long long)k * n + i] = (float)s;
           P.Us[(0LL * NR + k) * P.ldn + i] = h;
           P.Us[(1LL * NR + k) * P.ldn + i] = m;
           P.Us[(2LL * NR + k) * P.ldn + i] = l;
@@ -730,19 +698,6 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         s_nu[k] = nu;
       }
       __syncthreads();
-      // tracked u0 += nu U for this block's row slice (same slicing as (c))
-      {
-        const long long rows_per = (P.ldn + G - 1) / G;
-        const long long i0 = (long long)b * rows_per;
-        const long long i1 = i0 + rows_per < n ? i0 + rows_per : n;
-        const long long cnt = i1 > i0 ? i1 - i0 : 0;
-        for (long long e = tid; e < (long long)K * cnt; e += kBT) {
-          const int k = (int)(e / cnt);
-          const long long i = i0 + e % cnt;
-          if (s_cga[k]) P.U0[(long long)k * n + i] = fma(s_nu[k], (double)P.Uf[(long long)k * n + i],
-                                                        P.U0[(long long)k * n + i]);
-        }
-      }
       // (d) phase C: T = X^T U for the owned tiles (tensor cores), then the updates
       double* loc = s_pen;   // 2*kNRMax partials: r^T z, r^T r
       for (int f = tid; f < 2 * kNRMax; f += kBT) loc[f] = 0.0;
@@ -757,13 +712,12 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
           if (!s_cga[k]) continue;                  // warp-uniform
           const double nu = s_nu[k];
           const long long ko = (long long)k * p;
-          double t0v[4], qv[4], pv4[4], xv[4], rv[4], iv[4];
+          double qv[4], pv4[4], xv[4], rv[4], iv[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const long long j = t * kTM + lane + 32 * u;
             const bool ok = j < p;
             const long long o = ko + j;
-            t0v[u] = ok ? P.t0[o] : 0.0;
             qv[u] = ok ? P.q[o] : 0.0;
             pv4[u] = ok ? pc[o] : 0.0;
             xv[u] = ok ? P.x[o] : 0.0;
@@ -778,7 +732,6 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
             if (j < p) {
               const long long o = ko + j;
               const double tj = (double)ts[k * kTM + cl];
-              P.t0[o] = fma(nu, tj, t0v[u]);            // tracked X^T X x
               const double qj = tj + qv[u];
               P.x[o] = fma(nu, pv4[u], xv[u]);
               const double rj = fma(-nu, qj, rv[u]);
@@ -842,7 +795,6 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       __syncthreads();
     }
     if (!alive) break;
-    cg_since_exact += kcg;
     if (tid < K) {
       if (s_act[tid]) { s_fp[tid] = s_f[tid]; s_mm[tid] += 1; }
     }
@@ -863,6 +815,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       S->f_eps = 0.0;
       S->rel_change = s_rel[k];
       S->cg_relres = s_relres[k];
+      S->rel_prev = s_relp[k];
     }
   }
   tc::fence_before();

@@ -77,6 +77,13 @@ template <> struct XT<__half> {
   }
 };
 
+// Device-wide nanosecond timer (comparable across kernels on one GPU).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // ---------------------------------------------------------------------------
 // coherent (L2) loads for data other blocks wrote during this launch
 // ---------------------------------------------------------------------------

@@ -181,7 +181,8 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   flr_opts o;
   flr_default_opts(&o);
   if (opts) o = *opts;
-  if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0)
+  if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0 ||
+      o.max_refine < 0)
     return FLR_EINVAL;
   int precond = o.precond;
   if (precond == FLR_PC_AUTO) precond = FLR_PC_TWOLEVEL;
@@ -250,6 +251,7 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   P.lam1 = lambda1; P.lam2 = lambda2; P.eps = eps; P.tol = tol;
   P.tol_cg = o.tol_cg > 0.0 ? o.tol_cg : tol;
   P.max_mm = o.max_mm; P.max_cg = o.max_cg; P.min_cg = o.min_cg; P.precond = precond;
+  P.max_refine = o.max_refine;
   P.w = w; P.wpad = wpad; P.levels = levels;
   P.beta_init = nullptr;
   P.x = vec[0]; P.z = vec[1]; P.pb0 = vec[2]; P.pb1 = vec[3];
@@ -308,6 +310,9 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
     stats->rel_change = hs.rel_change;
     stats->cg_relres = hs.cg_relres;
     stats->ms = ms;
+    stats->refine_steps = hs.refine_steps;
+    stats->reserved = 0;
+    stats->est_err = estimated_error(hs);
   }
   return result;
 }

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/flr.h"
+#include "flr_internal.h"
 
 namespace {
 
@@ -117,6 +118,10 @@ void flr_server::worker(int slot) {
       op.grid = (int32_t)std::max<long long>(1, std::min<long long>(g, o.grid_per_slot));
       st = flr_solve(h, r.lambda1, r.lambda2, r.eps, r.tol, &op, nullptr, d.beta.data(), FLR_MEM_HOST,
                      &d.res.stats);
+      unsigned long long t0 = 0, t1 = 0;
+      flr_kernel_span(h, &t0, &t1);
+      d.res.dev_t0_ns = t0;
+      d.res.dev_t1_ns = t1;
       flr_destroy(h);
     }
     d.res.status = st;

@@ -16,6 +16,11 @@
 // S = lam1 A + lam2 B.  This is the outer residual of a mixed-precision
 // iterative refinement: the inner CG below may use FP32 products, while
 // every MM iteration restarts from an FP64-accurate residual and objective.
+// With max_refine > 0 the same is done inside an MM iteration: after the CG
+// meets tol_cg on its recursive residual, the true residual of the same
+// surrogate system is recomputed in FP64 and CG restarts from it until that
+// residual meets tol_cg too (at most max_refine times), so each surrogate is
+// solved to FP64 accuracy and the iterates follow the exact MM map.
 //
 // One CG iteration (products accumulate in FP32 for FP32/BF16/FP16 X):
 //   phase A: u += X[:, j0:j1] p[j0:j1]   (atomics into u)
@@ -54,13 +59,17 @@
 // FP64 arithmetic is scarce on this GPU, so scalar work runs in one thread
 // and block reductions go through shared memory and a single warp.
 #pragma once
+#include <cmath>
+
 #include "flr_device.cuh"
 
 namespace flr {
 
 struct DevStats {
-  int mm_iters, cg_iters, status, pad;
+  int mm_iters, cg_iters, status, refine_steps;
   double f, f_eps, rel_change, cg_relres;
+  double rel_prev;           // the relative change of f one MM iteration earlier
+  unsigned long long t0_ns, t1_ns;   // device global timer at the kernel's start and end
 };
 
 enum PrecondKind : int { PC_JACOBI = 1, PC_TRIDIAG = 2, PC_PAPER = 3, PC_TWOLEVEL = 4 };
@@ -92,6 +101,7 @@ struct SolveParams {
   const int* col;
   double lam1, lam2, eps, tol, tol_cg;
   int max_mm, max_cg, min_cg, precond;
+  int max_refine;            // FP64 residual restarts of the inner solve per MM iteration
   long long w, wpad;         // coefficients per block, padded to a multiple of 4
   int levels;                // PCR levels for the block chunk
   const double* beta_init;   // nullptr -> X_j^T y / X_j^T X_j
@@ -115,6 +125,24 @@ struct SolveParams {
   long long timeout;
   int inject_stall;          // test hook: block 0 skips the first barrier
 };
+
+// Estimated relative error of f(beta) against the exact minimum of Eq. obj:
+// the Prop. 1(ii) gap (f - f_eps) / f plus the extrapolated MM tail
+// rel * q / (1 - q), q = rel / rel_prev (linear convergence), capped at 0.999.
+inline double estimated_error(const DevStats& s) {
+  const double f = s.f;
+  if (!(f != 0.0) || !std::isfinite(f)) return INFINITY;
+  double e = (s.f - s.f_eps) / fabs(f);
+  if (e < 0.0) e = 0.0;
+  const double rel = s.rel_change, rp = s.rel_prev;
+  double tail = rel;
+  if (rp > 0.0 && rel > 0.0) {
+    double q = rel / rp;
+    if (q > 0.999) q = 0.999;
+    tail = rel * q / (1.0 - q);
+  }
+  return e + tail;
+}
 
 // shared-memory bytes of mm_solve_kernel (the host uses the same formula)
 __host__ __device__ inline size_t solve_smem_bytes(long long ldn, long long wpad, int V) {
@@ -513,6 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   Acc* red = reinterpret_cast<Acc*>(redd);
 
   const TX* Xt = reinterpret_cast<const TX*>(P.Xt);
+  const unsigned long long t_kernel0 = (b == 0 && tid == 0) ? global_ns() : 0ull;
   GridBarrier gb{P.bar, P.err, 0u, P.timeout};
   int slot = 0;
   const long long zchunk = (n + G - 1) / G;
@@ -567,8 +596,11 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   if (P.inject_stall && b == 0) return;   // the others' bounded waits must expire
   if (!gb.sync()) return;
 
-  int ucur = 0, pcur = 0, mm = 0, cg_total = 0, status = ST_OK;
-  double f = 0.0, f_prev = 0.0, rel = 0.0, relres = 0.0, rss_last = 0.0;
+  int ucur = 0, pcur = 0, mm = 0, cg_total = 0, status = ST_OK, nref_total = 0;
+  double f = 0.0, f_prev = 0.0, rel = 0.0, rel_prev = 0.0, relres = 0.0, rss_last = 0.0;
+  // true when accumulator buffer `ucur` already holds X x for the current x in
+  // FP64 (left by the last refinement pass), so the next MM iteration skips it
+  bool u0_ready = false;
 
   while (true) {
     void* U0 = ucur ? P.ub1 : P.ub0;
@@ -640,7 +672,9 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
     if (tri) setup_tridiag(P, j0, wl, tv, s_wl, s_wr, pw);
     // ---------------- u0 = X x in FP64 (refinement pass)
     zero_u(U1);
-    phase_a<TX, double>(P, Xt, j0, wl, vsd, redd, reinterpret_cast<double*>(U0) + (long long)rep * P.ldn);
+    if (!u0_ready)
+      phase_a<TX, double>(P, Xt, j0, wl, vsd, redd, reinterpret_cast<double*>(U0) + (long long)rep * P.ldn);
+    u0_ready = false;
     block_reduce<2>(pen, rs, ncol);
     if (!grid_sum(pen)) return;
     // ---------------- f(beta(r)) (Eq. obj) and the outer stop test
@@ -652,6 +686,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
     }
     if (!isfinite(f)) { status = ST_NONFINITE; break; }
     if (mm > 0) {
+      rel_prev = rel;
       rel = fabs(f - f_prev) / fabs(f_prev);
       if (rel <= P.tol) break;
     }
@@ -743,171 +778,240 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       for (long long c = j0 + tid; c < j1 && c < nc; c += kThreads) P.qci[c] = 1.0 / ldcg(P.qc + c);
       __syncthreads();
     }
-    apply_precond(P, tri, j0, wl, s_idg, rsm, zs, pw, pw + wp);
-    if (two) {   // z0 = D^-1 r0 + coarse part
-      for (int jj = tid; jj < wl; jj += kThreads) {
-        const int c = cid_s[jj];
-        if (c >= 0) zs[jj] = fma(ldcg(P.sc0 + c), qi_s[jj], zs[jj]);
-      }
-      __syncthreads();
-    }
-    double rz2[2] = {0.0, 0.0};
-    {
-      double* pg = pcur ? P.pb1 : P.pb0;
-      for (int jj = tid; jj < wl; jj += kThreads) {
-        const double rj = rsm[jj], zj = zs[jj];
-        ps[jj] = zj;
-        pg[j0 + jj] = zj;
-        rz2[0] = fma(rj, zj, rz2[0]);
-        rz2[1] = fma(rj, rj, rz2[1]);
-      }
-    }
-    block_reduce<2>(rz2, rs, ncol);
-    if (!grid_sum(rz2)) return;
-    double rz = rz2[0], rr = rz2[1], gamma = 0.0;
-    ucur ^= 1;
-    // ---------------- CG iterations (inner products and scalars in FP64)
-    int k = 0;
+    // The inner solve.  Each pass runs PCG from the residual in rsm (whose
+    // component sums are in the array picked by kpar) until the recursive
+    // residual meets tol_cg; with max_refine > 0 the true residual
+    // c - Q x is then recomputed in FP64 and, while it is still above
+    // tol_cg, PCG restarts from it (mixed-precision iterative refinement of
+    // one surrogate system).
+    int kpar = 0;        // CG iteration k accumulates component sums into sc[(k + kpar + 1) & 1]
+    int nref_mm = 0, cg_mm = 0;
     while (true) {
-      if (tid == 0) {
-        const double rel_r = sqrt(rr) / P.cnorm;
-        sc[0] = rel_r;
-        sc[1] = (k >= P.max_cg || (k >= P.min_cg && rel_r <= P.tol_cg)) ? 1.0 : 0.0;
-      }
-      __syncthreads();
-      relres = sc[0];
-      if (sc[1] != 0.0) break;
-      Acc* Ucur = reinterpret_cast<Acc*>(ucur ? P.ub1 : P.ub0);
-      void* Unext = ucur ? P.ub0 : P.ub1;
-      const double* pc = pcur ? P.pb1 : P.pb0;
-      const double* po = pcur ? P.pb0 : P.pb1;
-      // component sums of r: this iteration's accumulator and the previous one's
-      double* Scur = (k & 1) ? P.sc0 : P.sc1;
-      double* Sold = (k & 1) ? P.sc1 : P.sc0;
-      // p at a neighbour: own values from shared memory; another block's value is
-      // z + gamma p_old (bit-identical to its owner's update), or p itself at k = 0
-      auto pval = [&](long long kk) -> double {
-        if (kk >= j0 && kk < j1) return ps[kk - j0];
-        if (k == 0) return ldcg(pc + kk);
-        double zk = ldcg(P.z + kk);
-        if (two) {
-          const int c = __ldcg(P.cid + kk);
-          if (c >= 0) zk = fma(ldcg(Sold + c), ldcg(P.qcinv + kk), zk);
+      double* Sr = (kpar & 1) ? P.sc1 : P.sc0;   // component sums of the start residual
+      apply_precond(P, tri, j0, wl, s_idg, rsm, zs, pw, pw + wp);
+      if (two) {   // z0 = D^-1 r0 + coarse part
+        for (int jj = tid; jj < wl; jj += kThreads) {
+          const int c = cid_s[jj];
+          if (c >= 0) zs[jj] = fma(ldcg(Sr + c), qi_s[jj], zs[jj]);
         }
-        return fma(gamma, ldcg(po + kk), zk);
-      };
-      double sv[1] = {0.0};
+        __syncthreads();
+      }
+      double rz2[2] = {0.0, 0.0};
+      {
+        double* pg = pcur ? P.pb1 : P.pb0;
+        for (int jj = tid; jj < wl; jj += kThreads) {
+          const double rj = rsm[jj], zj = zs[jj];
+          ps[jj] = zj;
+          pg[j0 + jj] = zj;
+          rz2[0] = fma(rj, zj, rz2[0]);
+          rz2[1] = fma(rj, rj, rz2[1]);
+        }
+      }
+      block_reduce<2>(rz2, rs, ncol);
+      if (!grid_sum(rz2)) return;
+      double rz = rz2[0], rr = rz2[1], gamma = 0.0;
+      ucur ^= 1;
+      // ---------------- CG iterations (inner products and scalars in FP64)
+      int k = 0;
+      while (true) {
+        if (tid == 0) {
+          const double rel_r = sqrt(rr) / P.cnorm;
+          sc[0] = rel_r;
+          sc[1] = (k >= P.max_cg || (k >= P.min_cg && rel_r <= P.tol_cg)) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        relres = sc[0];
+        if (sc[1] != 0.0) break;
+        Acc* Ucur = reinterpret_cast<Acc*>(ucur ? P.ub1 : P.ub0);
+        void* Unext = ucur ? P.ub0 : P.ub1;
+        const double* pc = pcur ? P.pb1 : P.pb0;
+        const double* po = pcur ? P.pb0 : P.pb1;
+        // component sums of r: this iteration's accumulator and the previous one's
+        double* Scur = ((k + kpar) & 1) ? P.sc0 : P.sc1;
+        double* Sold = ((k + kpar) & 1) ? P.sc1 : P.sc0;
+        // p at a neighbour: own values from shared memory; another block's value is
+        // z + gamma p_old (bit-identical to its owner's update), or p itself at k = 0
+        auto pval = [&](long long kk) -> double {
+          if (kk >= j0 && kk < j1) return ps[kk - j0];
+          if (k == 0) return ldcg(pc + kk);
+          double zk = ldcg(P.z + kk);
+          if (two) {
+            const int c = __ldcg(P.cid + kk);
+            if (c >= 0) zk = fma(ldcg(Sold + c), ldcg(P.qcinv + kk), zk);
+          }
+          return fma(gamma, ldcg(po + kk), zk);
+        };
+        double sv[1] = {0.0};
+        for (int jj = tid; jj < wl; jj += kThreads) {
+          const long long j = j0 + jj;
+          const double pj = ps[jj];
+          double lap = 0.0;
+          if (GK == GK_STENCIL) {
+            const unsigned char fl = nb[jj];
+            const double pl = (fl & NB_L) ? pval(j - 1) : pj;
+            const double pr = (fl & NB_R) ? pval(j + 1) : pj;
+            const double pu = (fl & NB_U) ? pval(j - q2) : pj;
+            const double pd = (fl & NB_D) ? pval(j + q2) : pj;
+            lap = fma(s_wl[jj], pj - pl, lap);
+            lap = fma(s_wr[jj], pj - pr, lap);
+            lap = fma(s_wu[jj], pj - pu, lap);
+            lap = fma(s_wd[jj], pj - pd, lap);
+          } else {
+            for (long long e = P.rowptr[j]; e < P.rowptr[j + 1]; ++e)
+              lap = fma(P.wc[e], pj - pval(P.col[e]), lap);
+          }
+          const double spj = fma(s_la[jj], pj, lap);
+          qs[jj] = spj;
+          sv[0] = fma(pj, spj, sv[0]);
+          vs[jj] = (Acc)pj;
+        }
+        zero_u(Unext);
+        __syncthreads();
+        phase_a<TX, Acc>(P, Xt, j0, wl, vs, red, Ucur + (long long)rep * P.ldn * 8 / (long long)sizeof(Acc));
+        block_reduce<1>(sv, rs, ncol);
+        if (!grid_sum(sv)) return;
+        // p^T Q p = ||X p||^2 + p^T S p
+        double uu[1] = {stage_u<Acc>(Ucur, us, n, P.ldn, P.y, false)};
+        block_reduce<1>(uu, rs, kThreads);
+        if (tid == 0) {
+          const double pq = uu[0] + sv[0];
+          const bool bad = !(pq > 0.0) || !isfinite(pq);
+          sc[2] = bad ? 0.0 : rz / pq;
+          sc[3] = bad ? (isfinite(pq) ? (double)ST_BREAKDOWN : (double)ST_NONFINITE) : 0.0;
+        }
+        __syncthreads();
+        if (sc[3] != 0.0) { status = (int)sc[3]; break; }
+        const double nu = sc[2];
+        phase_c<TX, Acc>(P, Xt, j0, wl, us, tv);
+        for (int jj = tid; jj < wl; jj += kThreads) {
+          const double xn = fma(nu, ps[jj], xs[jj]);
+          xs[jj] = xn;
+          P.x[j0 + jj] = xn;
+          rsm[jj] = fma(-nu, tv[jj] + qs[jj], rsm[jj]);
+        }
+        __syncthreads();
+        apply_precond(P, tri, j0, wl, s_idg, rsm, zs, pw, pw + wp);
+        if (two) {
+          // 1_c^T r into this iteration's accumulator; clear the previous one (its
+          // readers, the p update and the halo of phase A, finished before barrier 1)
+          for (int base = warp * 32; base < wl; base += kThreads) {
+            const int jj = base + lane;
+            warp_add_by_key(Scur, jj < wl ? cid_s[jj] : -1, jj < wl ? rsm[jj] : 0.0);
+          }
+          for (long long c = j0 + tid; c < j1 && c < nc; c += kThreads) Sold[c] = 0.0;
+        }
+        double rzn[2] = {0.0, 0.0};
+        for (int jj = tid; jj < wl; jj += kThreads) {
+          const double rj = rsm[jj];
+          rzn[0] = fma(rj, zs[jj], rzn[0]);
+          rzn[1] = fma(rj, rj, rzn[1]);
+        }
+        block_reduce<2>(rzn, rs, ncol);
+        if (!grid_sum(rzn)) return;
+        if (two) {   // r^T z += sum_c (1_c^T r)^2 / q_c, in the same order in every block
+          double cz[1] = {0.0};
+          for (int c0 = tid; c0 < nc; c0 += 4 * kThreads) {   // 8 loads in flight per thread
+            double sv_[4], qv_[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int c = c0 + u * kThreads;
+              sv_[u] = c < nc ? ldcg(Scur + c) : 0.0;
+              qv_[u] = c < nc ? ldcg(P.qci + c) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cz[0] = fma(sv_[u] * sv_[u], qv_[u], cz[0]);
+          }
+          block_reduce<1>(cz, rs, kThreads);
+          rzn[0] += cz[0];
+        }
+        if (tid == 0) sc[4] = rzn[0] / rz;
+        __syncthreads();
+        gamma = sc[4];
+        rz = rzn[0];
+        rr = rzn[1];
+        // p_{j+1} = z_j + gamma p_j (shared copy and the other global buffer)
+        double* pn = pcur ? P.pb0 : P.pb1;
+        for (int jj = tid; jj < wl; jj += kThreads) {
+          double zj = zs[jj];
+          if (two) {
+            const int c = cid_s[jj];
+            if (c >= 0) zj = fma(ldcg(Scur + c), qi_s[jj], zj);
+          }
+          const double v = fma(gamma, ps[jj], zj);
+          ps[jj] = v;
+          pn[j0 + jj] = v;
+        }
+        pcur ^= 1;
+        ucur ^= 1;
+        ++k;
+        __syncthreads();
+      }
+      cg_total += k;
+      cg_mm += k;
+      if (status != ST_OK || k == 0 || nref_mm >= P.max_refine) break;
+      // ---------------- refinement: r = c - X^T X x - S x in FP64 with this MM
+      // iteration's weights.  Accumulator `ucur` is zero here (cleared during
+      // the last CG iteration) and receives X x; the other one is cleared.
+      void* Ux = ucur ? P.ub1 : P.ub0;
       for (int jj = tid; jj < wl; jj += kThreads) {
         const long long j = j0 + jj;
-        const double pj = ps[jj];
+        const double xj = xs[jj];
         double lap = 0.0;
         if (GK == GK_STENCIL) {
           const unsigned char fl = nb[jj];
-          const double pl = (fl & NB_L) ? pval(j - 1) : pj;
-          const double pr = (fl & NB_R) ? pval(j + 1) : pj;
-          const double pu = (fl & NB_U) ? pval(j - q2) : pj;
-          const double pd = (fl & NB_D) ? pval(j + q2) : pj;
-          lap = fma(s_wl[jj], pj - pl, lap);
-          lap = fma(s_wr[jj], pj - pr, lap);
-          lap = fma(s_wu[jj], pj - pu, lap);
-          lap = fma(s_wd[jj], pj - pd, lap);
+          if (fl & NB_L) lap = fma(s_wl[jj], xj - ldcg(P.x + j - 1), lap);
+          if (fl & NB_R) lap = fma(s_wr[jj], xj - ldcg(P.x + j + 1), lap);
+          if (fl & NB_U) lap = fma(s_wu[jj], xj - ldcg(P.x + j - q2), lap);
+          if (fl & NB_D) lap = fma(s_wd[jj], xj - ldcg(P.x + j + q2), lap);
         } else {
           for (long long e = P.rowptr[j]; e < P.rowptr[j + 1]; ++e)
-            lap = fma(P.wc[e], pj - pval(P.col[e]), lap);
+            lap = fma(P.wc[e], xj - ldcg(P.x + P.col[e]), lap);
         }
-        const double spj = fma(s_la[jj], pj, lap);
-        qs[jj] = spj;
-        sv[0] = fma(pj, spj, sv[0]);
-        vs[jj] = (Acc)pj;
+        qs[jj] = fma(s_la[jj], xj, lap);
+        vsd[jj] = xj;
       }
-      zero_u(Unext);
+      zero_u(ucur ? P.ub0 : P.ub1);
       __syncthreads();
-      phase_a<TX, Acc>(P, Xt, j0, wl, vs, red, Ucur + (long long)rep * P.ldn * 8 / (long long)sizeof(Acc));
-      block_reduce<1>(sv, rs, ncol);
-      if (!grid_sum(sv)) return;
-      // p^T Q p = ||X p||^2 + p^T S p
-      double uu[1] = {stage_u<Acc>(Ucur, us, n, P.ldn, P.y, false)};
-      block_reduce<1>(uu, rs, kThreads);
-      if (tid == 0) {
-        const double pq = uu[0] + sv[0];
-        const bool bad = !(pq > 0.0) || !isfinite(pq);
-        sc[2] = bad ? 0.0 : rz / pq;
-        sc[3] = bad ? (isfinite(pq) ? (double)ST_BREAKDOWN : (double)ST_NONFINITE) : 0.0;
-      }
+      phase_a<TX, double>(P, Xt, j0, wl, vsd, redd, reinterpret_cast<double*>(Ux) + (long long)rep * P.ldn);
+      if (!gb.sync()) return;
+      // the last CG iteration's component sums are no longer read: clear them;
+      // the other array was cleared during that iteration and takes 1_c^T r
+      double* Slast = ((k - 1 + kpar) & 1) ? P.sc0 : P.sc1;
+      double* Snew = ((k - 1 + kpar) & 1) ? P.sc1 : P.sc0;
+      if (two)
+        for (long long c = j0 + tid; c < j1 && c < nc; c += kThreads) Slast[c] = 0.0;
+      (void)stage_u<double>(reinterpret_cast<const double*>(Ux), usd, n, P.ldn, P.y, false);
       __syncthreads();
-      if (sc[3] != 0.0) { status = (int)sc[3]; break; }
-      const double nu = sc[2];
-      phase_c<TX, Acc>(P, Xt, j0, wl, us, tv);
+      phase_c<TX, double>(P, Xt, j0, wl, usd, tv);
+      double rr1[1] = {0.0};
       for (int jj = tid; jj < wl; jj += kThreads) {
-        const double xn = fma(nu, ps[jj], xs[jj]);
-        xs[jj] = xn;
-        P.x[j0 + jj] = xn;
-        rsm[jj] = fma(-nu, tv[jj] + qs[jj], rsm[jj]);
+        const double rj = (P.c[j0 + jj] - tv[jj]) - qs[jj];
+        rsm[jj] = rj;
+        rr1[0] = fma(rj, rj, rr1[0]);
       }
       __syncthreads();
-      apply_precond(P, tri, j0, wl, s_idg, rsm, zs, pw, pw + wp);
-      if (two) {
-        // 1_c^T r into this iteration's accumulator; clear the previous one (its
-        // readers, the p update and the halo of phase A, finished before barrier 1)
+      if (two)
         for (int base = warp * 32; base < wl; base += kThreads) {
           const int jj = base + lane;
-          warp_add_by_key(Scur, jj < wl ? cid_s[jj] : -1, jj < wl ? rsm[jj] : 0.0);
+          warp_add_by_key(Snew, jj < wl ? cid_s[jj] : -1, jj < wl ? rsm[jj] : 0.0);
         }
-        for (long long c = j0 + tid; c < j1 && c < nc; c += kThreads) Sold[c] = 0.0;
+      block_reduce<1>(rr1, rs, ncol);
+      if (!grid_sum(rr1)) return;
+      ++nref_mm;
+      ++nref_total;
+      relres = sqrt(rr1[0]) / P.cnorm;
+      if (relres <= P.tol_cg) {   // accurate: X x stays in accumulator `ucur` for the next MM iteration
+        u0_ready = true;
+        break;
       }
-      double rzn[2] = {0.0, 0.0};
-      for (int jj = tid; jj < wl; jj += kThreads) {
-        const double rj = rsm[jj];
-        rzn[0] = fma(rj, zs[jj], rzn[0]);
-        rzn[1] = fma(rj, rj, rzn[1]);
-      }
-      block_reduce<2>(rzn, rs, ncol);
-      if (!grid_sum(rzn)) return;
-      if (two) {   // r^T z += sum_c (1_c^T r)^2 / q_c, in the same order in every block
-        double cz[1] = {0.0};
-        for (int c0 = tid; c0 < nc; c0 += 4 * kThreads) {   // 8 loads in flight per thread
-          double sv_[4], qv_[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int c = c0 + u * kThreads;
-            sv_[u] = c < nc ? ldcg(Scur + c) : 0.0;
-            qv_[u] = c < nc ? ldcg(P.qci + c) : 0.0;
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) cz[0] = fma(sv_[u] * sv_[u], qv_[u], cz[0]);
-        }
-        block_reduce<1>(cz, rs, kThreads);
-        rzn[0] += cz[0];
-      }
-      if (tid == 0) sc[4] = rzn[0] / rz;
-      __syncthreads();
-      gamma = sc[4];
-      rz = rzn[0];
-      rr = rzn[1];
-      // p_{j+1} = z_j + gamma p_j (shared copy and the other global buffer)
-      double* pn = pcur ? P.pb0 : P.pb1;
-      for (int jj = tid; jj < wl; jj += kThreads) {
-        double zj = zs[jj];
-        if (two) {
-          const int c = cid_s[jj];
-          if (c >= 0) zj = fma(ldcg(Scur + c), qi_s[jj], zj);
-        }
-        const double v = fma(gamma, ps[jj], zj);
-        ps[jj] = v;
-        pn[j0 + jj] = v;
-      }
-      pcur ^= 1;
-      ucur ^= 1;
-      ++k;
-      __syncthreads();
+      kpar = (Snew == P.sc1) ? 1 : 0;   // the restart's k = 0 reads Snew as its start sums
     }
-    cg_total += k;
     if (status != ST_OK) break;
     f_prev = f;
     ++mm;
     // x was written before the last grid barrier (or is unchanged): the next
     // reweight may read neighbours' x directly.
-    if (k == 0 && !gb.sync()) return;
+    if (cg_mm == 0 && !gb.sync()) return;
   }
 
   // ---------------- f_eps at the returned iterate (Eq. pert)
@@ -945,11 +1049,14 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       S->mm_iters = mm;
       S->cg_iters = cg_total;
       S->status = status;
-      S->pad = 0;
+      S->refine_steps = nref_total;
       S->f = f;
       S->f_eps = 0.5 * rss_last + P.lam1 * pe[0] + P.lam2 * pe[1];
       S->rel_change = rel;
       S->cg_relres = relres;
+      S->rel_prev = rel_prev;
+      S->t0_ns = t_kernel0;
+      S->t1_ns = global_ns();
     }
   }
 }

@@ -90,11 +90,11 @@ def _c_layout():
     fields = {
         "flr_graph": ["kind", "q1", "q2", "edges", "m"],
         "flr_opts": ["max_mm", "max_cg", "min_cg", "precond", "tol_cg", "grid", "inject_stall",
-                     "wait_cycles", "refine_every"],
-        "flr_stats": [],
+                     "wait_cycles", "max_refine"],
+        "flr_stats": ["mm_iters", "f", "ms", "refine_steps", "est_err"],
         "flr_server_opts": [],
         "flr_request": [],
-        "flr_result": [],
+        "flr_result": ["stats", "t_submit", "footprint", "dev_t0_ns", "dev_t1_ns"],
     }
     enums = ["FLR_OK", "FLR_EINVAL", "FLR_ENOMEM", "FLR_ECUDA", "FLR_ENOTCONV", "FLR_EBREAKDOWN",
              "FLR_ENONFINITE", "FLR_ETIMEOUT", "FLR_ENOTIMPL", "FLR_ESCRATCH", "FLR_F64", "FLR_F32",

@@ -1,10 +1,21 @@
 """GPU parity: the CUDA MM/PCG solve (through the C ABI) against the FP64 oracle.
 
-Parity bar: relative objective gap |f_gpu - f_oracle| / f_oracle <= 1e-6, and,
-when both sides run the MM to a tight stop, max |beta_gpu - beta_oracle| <=
-1e-4 max |beta_oracle|.  Oracle values come from tests/golden/*.json (written
-by tests/golden/make_golden.py, which calls only oracle/) or from running the
-oracle inline on small cases.
+Parity bar: relative objective gap |f_gpu - f_oracle| / f_oracle <= 1e-6, and
+max |beta_gpu - beta_oracle| <= 1e-4 max |beta_oracle|.  Oracle values come
+from tests/golden/*.json (written by tests/golden/make_golden.py, which calls
+only oracle/) or from running the oracle inline on small cases.
+
+Two kinds of comparison:
+  * converged: both sides run the MM to their stop rule; the objective gap is
+    checked, and beta where both stops are tight;
+  * iterates: both sides run exactly R MM iterations from the same start
+    (Algorithm 1's map is deterministic) and beta(R), f(beta(R)) are
+    compared.  The GPU solves every surrogate to FP64 accuracy here
+    (max_refine > 0: CG restarts from the FP64 true residual until it meets
+    tol_cg).  This checks beta at the 1e-4 bar on p > n problems too, where
+    f_eps is strictly convex but so flat along some directions (curvature
+    lam1 eps / (|b| + eps)^2) that beta at a given objective gap is not
+    determined to 1e-4 by the gap alone.
 """
 import json
 import os
@@ -70,6 +81,26 @@ def assert_parity(st, beta, f_ref, beta_ref, check_beta=True):
         assert db <= BETA, (db, st)
 
 
+# exact-map settings: each surrogate solved to an FP64 true residual of 1e-12
+EXACT = dict(tol_cg=1e-12, max_refine=20, max_cg=20000)
+
+
+def assert_iterate(flr, prob, pr, g, **kw):
+    """The GPU's beta(R), f(beta(R)) after exactly R MM iterations equal the oracle's."""
+    R = g["fixed_iterations"]
+    opts = dict(EXACT)
+    opts.update(kw)
+    beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-300, max_mm=R, **opts)
+    assert st.status == flr.FLR_ENOTCONV and st.mm_iters == R, st
+    b = beta.cpu().numpy()
+    ref = np.array(g["beta"])
+    db = np.abs(b - ref).max() / np.abs(ref).max()
+    assert db <= BETA, (db, st)
+    assert abs(st.f - g["f"]) <= 1e-10 * abs(g["f"]), (st.f, g["f"])
+    assert st.refine_steps > 0 and st.cg_relres <= 1e-12, st
+    return db, st
+
+
 # --------------------------------------------------------------------------- configurations
 @pytest.mark.parametrize("precond", ["tridiag", "jacobi", "paper", "twolevel"])
 def test_config1_chain_f64(flr, precond):
@@ -80,6 +111,15 @@ def test_config1_chain_f64(flr, precond):
     beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-12, precond=precond,
                           max_mm=20000, tol_cg=1e-12)
     assert_parity(st, beta, g["f"], np.array(g["beta"]))
+    # the stated error covers the perturbation gap of Prop. 1(ii) at the returned
+    # beta (oracle arithmetic) and the actual gap to the oracle's converged objective
+    b = beta.cpu().numpy()
+    X, E = pr.X64(), pr.graph.edges
+    f_b = mm.objective(X, pr.y, b, pr.lam1, pr.lam2, E)
+    fe_b = mm.objective_eps(X, pr.y, b, pr.lam1, pr.lam2, E, pr.eps)
+    assert st.est_err * abs(f_b) >= f_b - fe_b >= 0.0, (st.est_err, f_b, fe_b)
+    assert st.est_err >= abs(st.f - g["f"]) / g["f"], (st.est_err, st.f, g["f"])
+    assert abs(st.f_eps - fe_b) <= 1e-10 * abs(fe_b)
 
 
 @pytest.mark.parametrize("grid", [1, 2, 3, 7, 13])
@@ -105,25 +145,31 @@ def test_config2_lattice_f32_small(flr):
 
 @pytest.mark.parametrize("precond", ["jacobi", "tridiag", "twolevel"])
 def test_config2_lattice_q40(flr, precond):
+    """q = 40 lattice (p = 1600, n = 160, FP32): the converged objective at the
+    bench's stop settings, and the MM iterates after 300 iterations (beta at
+    1e-4), for every preconditioner."""
     g = golden("config2_q40")
     pr = fi.config(2, scale=0.16)
     check_fingerprint(pr, g)
     prob = problem(flr, pr)
     beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-9, precond=precond,
                           tol_cg=1e-8, max_mm=20000)
-    assert_parity(st, beta, g["f"], np.array(g["beta"]), check_beta=False)
+    assert st.status == 0 and abs(st.f - g["f"]) / g["f"] <= GAP, (st, g["f"])
+    assert_iterate(flr, prob, pr, golden("config2_q40_r300"), precond=precond)
 
 
 def test_twolevel_cuts_cg_iterations(flr):
-    """The coarse correction on fused groups: same answer, several times fewer CG iterations."""
+    """The coarse correction on fused groups: the same objective with several
+    times fewer CG iterations (beta parity of both preconditioners is checked
+    on the iterates by test_config2_lattice_q40)."""
     g = golden("config2_q40")
     pr = fi.config(2, scale=0.16)
     prob = problem(flr, pr)
     kw = dict(eps=pr.eps, tol=1e-9, tol_cg=1e-8, max_mm=20000)
     bj, sj = prob.solve(pr.lam1, pr.lam2, precond="jacobi", **kw)
     bt, st = prob.solve(pr.lam1, pr.lam2, precond="twolevel", **kw)
-    assert_parity(sj, bj, g["f"], np.array(g["beta"]), check_beta=False)
-    assert_parity(st, bt, g["f"], np.array(g["beta"]), check_beta=False)
+    for s_ in (sj, st):
+        assert s_.status == 0 and abs(s_.f - g["f"]) / g["f"] <= GAP, (s_, g["f"])
     assert 3 * st.cg_iters < sj.cg_iters, (st.cg_iters, sj.cg_iters)
 
 
@@ -138,19 +184,15 @@ def test_config4_lattice_f16_small(flr):
 
 def test_config4_q50x80_against_oracle(flr):
     """The config-4 generator at 50x80 (p=4000, n=200, FP16 AR(1) rows) against the
-    stored Woodbury-oracle solve.  p = 20 n: the minimiser is flat along many
-    directions and the MM needs ~10^4 iterations, so at equal objective (gap
-    ~1e-9) beta differs by ~2e-4 of its scale; the objective decides, and beta
-    is held to 1e-3."""
+    Woodbury oracle: the converged objective, and the MM iterates after 300
+    iterations with beta at 1e-4."""
     g = golden("config4_q50x80")
     pr = fi.config(4, scale=0.04)
     check_fingerprint(pr, g)
     prob = problem(flr, pr)
     beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-12, tol_cg=1e-10, max_mm=20000)
-    assert_parity(st, beta, g["f"], np.array(g["beta"]), check_beta=False)
-    b = beta.cpu().numpy()
-    ref = np.array(g["beta"])
-    assert np.abs(b - ref).max() <= 1e-3 * np.abs(ref).max()
+    assert st.status == 0 and abs(st.f - g["f"]) / g["f"] <= GAP, (st, g["f"])
+    assert_iterate(flr, prob, pr, golden("config4_q50x80_r300"))
 
 
 def test_config4_full_size_is_stationary(flr):
@@ -188,7 +230,10 @@ def test_bf16_chain_against_inline_oracle(flr):
 
 
 def test_config2_full_size(flr):
-    """The bench workload (q=100 lattice, n=1000, FP32) against the stored oracle solve."""
+    """The bench workload (q=100 lattice, n=1000, FP32) against the oracle: the
+    objective gap at the bench's own stop settings (tol 1e-9, tol_cg 1e-8, no
+    refinement restarts), and every coefficient of the MM iterate after 200
+    iterations at 1e-4 of max |beta|."""
     g = golden("config2")
     pr = fi.config(2)
     check_fingerprint(pr, g)
@@ -196,10 +241,37 @@ def test_config2_full_size(flr):
     beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-9, tol_cg=1e-8, max_mm=20000)
     gap = abs(st.f - g["f"]) / g["f"]
     assert st.status == 0 and gap <= GAP, (gap, st)
-    b = beta.cpu().numpy()
-    idx = np.array(g["beta_idx"])
-    db = np.abs(b[idx] - np.array(g["beta_sample"])).max() / g["beta_absmax"]
-    assert db <= 1e-2, db
+    assert st.est_err >= gap, (st.est_err, gap)
+    assert_iterate(flr, prob, pr, golden("config2_r200"))
+
+
+@pytest.mark.parametrize("p", [1000, 10000])
+def test_paper_c1_mm_iterations_match_table_c1(flr, p):
+    """Scenario C1 of Section 5 regenerated (n = 1000, FP64 X, eps = 1e-8, stop at a
+    relative change of f below 1e-5) solved on the GPU: the MM iteration count
+    lands within 20 % of the paper's Table C.1 average (23.0 at p = 1000, 83.9 at
+    p = 10^4; lam = (0.1, 0.1)), as the oracle's does.  The paper's random draws
+    are not ours, so this is a plausibility pin on the whole MM, not parity."""
+    with open(os.path.join(GOLD, "paper_table_c1.json")) as fh:
+        tab = json.load(fh)
+    row = [r for r in tab["rows"] if r["p"] == p and r["lam1"] == 0.1 and r["lam2"] == 0.1][0]
+    pr = fi.paper_scenario(1, p, n=tab["n"], lam1=0.1, lam2=0.1, eps=tab["eps"])
+    prob = problem(flr, pr)
+    _, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=tab["tol"], tol_cg=1e-10, max_refine=4,
+                       max_mm=20000, max_cg=50000)
+    assert st.status == 0, st
+    assert abs(st.mm_iters - row["mm_iters"]) <= 0.2 * row["mm_iters"], (st.mm_iters, row)
+
+
+def test_paper_c1_p200_against_oracle(flr):
+    """Scenario C1 at p = 200 (n = 1000, FP64 X, eps = 1e-6) against the stored oracle solve."""
+    g = golden("paper_c1_p200")
+    pr = fi.paper_scenario(1, 200, eps=1e-6)
+    check_fingerprint(pr, g)
+    prob = problem(flr, pr)
+    beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-13, tol_cg=1e-12, max_refine=4,
+                          max_mm=20000)
+    assert_parity(st, beta, g["f"], np.array(g["beta"]))
 
 
 # --------------------------------------------------------------------------- special cases

@@ -3,8 +3,11 @@
 Requests of mixed p, n, dtype and edge set (chain, lattice, 5-NN graph; the
 served-stream recipe at reduced p) go through a 4-slot server.  Each result
 must equal the same problem solved alone through flr_solve with the same
-block count (within the parity tolerances), the server must have run solves
-concurrently, and it must refuse what cannot fit or is malformed.
+block count (objective to 1e-8, beta to 1e-4 of max |beta|), the solve
+kernels of at least two requests must have overlapped on the GPU (device
+global-timer spans), and the server must refuse what cannot fit or is
+malformed.  Every surrogate is solved to FP64 accuracy (max_refine), so a
+request follows the exact MM map whatever else shares the GPU.
 """
 import numpy as np
 import pytest
@@ -37,33 +40,29 @@ def test_mixed_stream_equals_alone(flr):
     slots, gps = 4, 16
     srv = flr.Server(slots=slots, grid_per_slot=gps)
     ids = []
+    kw = dict(tol_cg=1e-12, max_refine=20, max_mm=30000)
     for r, pr in zip(reqs, probs):
         X, y = host_X(pr)
         ids.append(srv.submit(X, y, pr.graph, r.lam1, r.lam2, eps=pr.eps, tol=1e-11,
-                              dtype="bf16" if pr.dtype == "bf16" else None, tol_cg=1e-10,
-                              max_mm=30000))
+                              dtype="bf16" if pr.dtype == "bf16" else None, **kw))
     out = [srv.wait(i) for i in ids]
     srv.close()
     spans = []
     for (beta, res), r, pr in zip(out, reqs, probs):
         assert res.status == 0, (r, res.status)
-        spans.append((res.t_start, res.t_end))
+        assert 0 < res.dev_t0_ns < res.dev_t1_ns, (res.dev_t0_ns, res.dev_t1_ns)
+        spans.append((res.dev_t0_ns, res.dev_t1_ns))
         X, y = host_X(pr)
         alone = flr.Problem(X.cuda(), y.cuda(), pr.graph,
                             dtype="bf16" if pr.dtype == "bf16" else None)
         g = min(gps, max(1, -(-pr.n * pr.p // 65536)))
-        b1, s1 = alone.solve(r.lam1, r.lam2, eps=pr.eps, tol=1e-11, tol_cg=1e-10, max_mm=30000,
-                             grid=g)
-        # The objective decides (p > n: f is convex, not strictly).  Along the
-        # flat directions of such a request the FP64 atomics' run-dependent
-        # summation order moves beta by up to ~1e-4 of its scale at equal f,
-        # so beta is held to 1e-3.
+        b1, s1 = alone.solve(r.lam1, r.lam2, eps=pr.eps, tol=1e-11, grid=g, **kw)
         assert abs(res.stats.f - s1.f) <= 1e-8 * abs(s1.f), (r, res.stats.f, s1.f)
         db = np.abs(beta - b1.cpu().numpy()).max() / max(np.abs(beta).max(), 1e-300)
-        assert db <= 1e-3, (r, db)
-    # at least two solves were on the GPU at the same time
+        assert db <= 1e-4, (r, db)
+    # the solve kernels of at least two requests ran on the GPU at the same time
     spans.sort()
-    assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+    assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1)), spans
 
 
 def test_refuses_oversized_and_malformed(flr):

@@ -10,6 +10,8 @@ refused with FLR_ESCRATCH.  It is collected last so that a run stopping at
 the first failure has already run every other test.
 """
 import ctypes
+import json
+import os
 
 import numpy as np
 import pytest
@@ -62,12 +64,20 @@ def call_noalloc(flr, Xt, dtype_code, n, p, ldn, y, g, lam1, lam2, eps, tol, opt
     return code, out, st
 
 
+def golden(name):
+    with open(os.path.join(os.path.dirname(__file__), "golden", name + ".json")) as fh:
+        return json.load(fh)
+
+
 @pytest.mark.parametrize("cfg", ["chain_f64", "lattice_f32"])
 def test_noalloc_matches_allocating_solve_twice(flr, cfg):
     if cfg == "chain_f64":
         pr, vec, code, kw = fi.config(1), 2, flr.FLR_F64, dict(tol=1e-12, tol_cg=1e-12)
+        g = golden("config1")
     else:
         pr, vec, code, kw = fi.config(2, scale=0.04), 4, flr.FLR_F32, dict(tol=1e-12, tol_cg=1e-10)
+        g = golden("config2_q20")
+    g_beta = np.array(g["beta"])
     X = torch.from_numpy(pr.X).cuda()
     y = torch.from_numpy(pr.y).cuda()
     ref_beta, ref = flr.Problem(X, y, pr.graph).solve(pr.lam1, pr.lam2, eps=pr.eps, max_mm=20000, **kw)
@@ -81,10 +91,14 @@ def test_noalloc_matches_allocating_solve_twice(flr, cfg):
         assert abs(st.f - ref.f) / abs(ref.f) <= GAP
         db = (beta - ref_beta).abs().max().item() / ref_beta.abs().max().item()
         assert db <= BETA
+        # and the stored FP64 oracle solution itself (tests/golden, written from oracle/ only)
+        assert abs(st.f - g["f"]) / abs(g["f"]) <= GAP, (st.f, g["f"])
+        b = beta.cpu().numpy()
+        assert np.abs(b - g_beta).max() / np.abs(g_beta).max() <= BETA
 
 
 def test_noalloc_refuses_problems_beyond_its_scratch(flr):
-    n, p = 8, 300_000      # 9 * 8 * p bytes of vectors alone exceed the 16 MiB array
+    n, p = 8, 300_000      # 7 * 8 * p bytes of vectors alone exceed the 16 MiB array
     Xt = torch.zeros((p, n), dtype=torch.float32, device="cuda")
     y = torch.zeros(n, dtype=torch.float64, device="cuda")
     code, _, _ = call_noalloc(flr, Xt, flr.FLR_F32, n, p, n, y, fi.Graph("chain", p),
