@@ -351,6 +351,47 @@ class Request:
     seed: int
 
 
+@dataclasses.dataclass
+class DenoiseProblem:
+    """An FLSA instance (X = I, n = p): a noisy image y on a q1 x q2 lattice."""
+    name: str
+    y: np.ndarray
+    image: np.ndarray          # the noise-free image, row-major (q1 * q2,)
+    graph: Graph
+    lam1: float
+    lam2: float
+    eps: float
+
+    @property
+    def p(self) -> int:
+        return int(self.y.shape[0])
+
+
+def image_pattern(q1: int, q2: int) -> np.ndarray:
+    """A piecewise-constant test image with values in [0, 1], row-major: background
+    0.2, a disc of 0.9, a square of 0.5 and a bar of 1.0, placed at fixed fractions
+    of the frame (our choice; the image the paper denoises is not available)."""
+    r = (np.arange(q1)[:, None] + 0.5) / q1
+    c = (np.arange(q2)[None, :] + 0.5) / q2
+    img = np.full((q1, q2), 0.2)
+    img[(r - 0.3) ** 2 + (c - 0.35) ** 2 <= 0.2 ** 2] = 0.9
+    img[(r >= 0.6) & (r < 0.85) & (c >= 0.1) & (c < 0.4)] = 0.5
+    img[(r >= 0.15) & (r < 0.9) & (c >= 0.65) & (c < 0.8)] = 1.0
+    return img.reshape(-1)
+
+
+def denoise(q1: int = 256, q2: int = 256, s: int = 0, noise_sd: float = 0.3,
+            lam1: float = 0.0, lam2: float = 0.1, eps: float = 1e-6) -> DenoiseProblem:
+    """Image denoising as the two-dimensional FLSA (X = I; Section 5.2's image study
+    with its lambda = (0, 0.1) and (0, 1)): y = image + N(0, noise_sd^2), seed
+    1000 * 6 + s."""
+    img = image_pattern(q1, q2)
+    rng = np.random.default_rng(6000 + s)
+    y = img + noise_sd * rng.standard_normal(img.shape[0])
+    return DenoiseProblem(f"denoise-{q1}x{q2}-s{s}", y, img, Graph("lattice", q1 * q2, q1, q2),
+                          lam1, lam2, eps)
+
+
 def served_stream(count: int, seed: int = 5000, p_lo: int = 500, p_hi: int = 50000):
     """Request descriptors of the served mixed stream (Poisson arrivals at rate 1).
 

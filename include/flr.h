@@ -49,8 +49,15 @@ typedef enum flr_status {
 } flr_status;
 
 /* Storage type of X.  Products with X accumulate in FP32 for F32/BF16/F16
- * and in FP64 for F64; every other quantity is FP64. */
-typedef enum flr_dtype { FLR_F64 = 0, FLR_F32 = 1, FLR_BF16 = 2, FLR_F16 = 3 } flr_dtype;
+ * and in FP64 for F64; every other quantity is FP64.
+ * FLR_IDENTITY: X = I with n = p, the fused lasso signal approximator (FLSA,
+ * the special case of Eq. obj named in Section 1; Section 5.2 denoises an
+ * image with it).  No matrix is passed (X = NULL, ldx ignored) and the solve
+ * reads none: every X product is the vector itself, so each CG iteration is
+ * the Laplacian stencil or CSR product and vector work only.  flr_create,
+ * flr_solve and flr_solve_batch (one solve per pair) accept it; the server
+ * and flr_solve_noalloc do not (FLR_EINVAL). */
+typedef enum flr_dtype { FLR_F64 = 0, FLR_F32 = 1, FLR_BF16 = 2, FLR_F16 = 3, FLR_IDENTITY = 4 } flr_dtype;
 
 /* Where the pointers passed to flr_create / flr_solve live. */
 typedef enum flr_mem { FLR_MEM_DEVICE = 0, FLR_MEM_HOST = 1 } flr_mem;
@@ -120,8 +127,19 @@ typedef struct flr_opts {
                             times, until the true residual meets tol_cg too.  This solves
                             each surrogate to FP64 accuracy from FP32/BF16/FP16 products, so
                             the iterates follow the MM map of Algorithm 1 (mixed-precision
-                            iterative refinement).  flr_solve and flr_solve_noalloc only. */
-    int32_t reserved[3];
+                            iterative refinement).  flr_solve_batch applies it per RHS. */
+    int32_t x_smem;      /* flr_solve / flr_solve_noalloc: 0 (default) keeps as many leading
+                            columns of each thread block's slab of X in shared memory as fit,
+                            copied once per solve, so the X products read them on chip every
+                            CG iteration; -1 streams every column from global memory. */
+    double tol_cg_rel;   /* adaptive inner tolerance (default 0 = off).  With theta = tol_cg_rel
+                            > 0, the inner solve of MM iteration r stops at
+                            max(tol_cg, theta * rel_r), rel_r the relative change of f that
+                            iteration's outer test just measured (theta at r = 0): early
+                            surrogates, whose solutions are far from the limit, are solved
+                            loosely, later ones to tol_cg.  Every CG iteration still lowers
+                            the surrogate g_eps from its warm start, so f_eps still decreases
+                            monotonically (Prop. 1, Lemma 2); the fixed point is unchanged. */
 } flr_opts;
 
 typedef struct flr_stats {
@@ -153,7 +171,8 @@ void flr_default_opts(flr_opts* opts);
 
 /* Create a problem handle.
  *   X      n x p design matrix, row-major, row stride ldx >= p elements,
- *          element type `dtype` (FLR_BF16 / FLR_F16: 16-bit patterns).
+ *          element type `dtype` (FLR_BF16 / FLR_F16: 16-bit patterns);
+ *          NULL with dtype FLR_IDENTITY (then n must equal p).
  *   y      n responses (double).
  *   E      edge set (see flr_graph); E->edges in the memory named by `mem`.
  *   mem    FLR_MEM_DEVICE or FLR_MEM_HOST: where X, y and E->edges live.

@@ -20,11 +20,12 @@ from . import _build
 
 FLR_OK, FLR_EINVAL, FLR_ENOMEM, FLR_ECUDA, FLR_ENOTCONV = 0, 1, 2, 3, 4
 FLR_EBREAKDOWN, FLR_ENONFINITE, FLR_ETIMEOUT, FLR_ENOTIMPL, FLR_ESCRATCH = 5, 6, 7, 8, 9
-FLR_F64, FLR_F32, FLR_BF16, FLR_F16 = 0, 1, 2, 3
+FLR_F64, FLR_F32, FLR_BF16, FLR_F16, FLR_IDENTITY = 0, 1, 2, 3, 4
 FLR_MEM_DEVICE, FLR_MEM_HOST = 0, 1
 FLR_E_CHAIN, FLR_E_LATTICE, FLR_E_EDGES = 0, 1, 2
 PRECOND = {"auto": 0, "jacobi": 1, "tridiag": 2, "paper": 3, "twolevel": 4}
-DTYPE_CODES = {"f64": FLR_F64, "f32": FLR_F32, "bf16": FLR_BF16, "f16": FLR_F16}
+DTYPE_CODES = {"f64": FLR_F64, "f32": FLR_F32, "bf16": FLR_BF16, "f16": FLR_F16,
+               "identity": FLR_IDENTITY}
 
 # every symbol declared in include/flr.h
 EXPORTS = ("flr_default_opts", "flr_strerror", "flr_create", "flr_solve", "flr_solve_batch",
@@ -42,7 +43,8 @@ class FlrOpts(ctypes.Structure):
     _fields_ = [("max_mm", ctypes.c_int32), ("max_cg", ctypes.c_int32), ("min_cg", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("tol_cg", ctypes.c_double), ("grid", ctypes.c_int32),
                 ("inject_stall", ctypes.c_int32), ("wait_cycles", ctypes.c_int64),
-                ("max_refine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("max_refine", ctypes.c_int32), ("x_smem", ctypes.c_int32),
+                ("tol_cg_rel", ctypes.c_double)]
 
 
 class FlrStats(ctypes.Structure):
@@ -219,31 +221,44 @@ class Problem:
     X (n x p, row-major) and y (n) are torch tensors on the GPU or on the
     host (pinned for asynchronous copies); both are copied by the library.
     For BF16/FP16 X pass a torch.bfloat16/float16 tensor, or raw 16-bit
-    patterns (int16/uint16) with dtype="bf16"/"f16".
+    patterns (int16/uint16) with dtype="bf16"/"f16".  X = None with
+    dtype="identity" is the FLSA (X = I, n = p = len(y)).
     """
 
     def __init__(self, X, y, graph, dtype: Optional[str] = None, stream=None):
         torch = _torch()
         lib = load()
-        if X.dim() != 2:
-            raise ValueError("X must be 2-D (n x p)")
-        if X.stride(1) != 1:
-            X = X.contiguous()
-        self.n, self.p = int(X.shape[0]), int(X.shape[1])
-        self.dtype = _dtype_code(X, dtype)
-        on_dev = X.is_cuda
-        y = y.to(device=X.device, dtype=torch.float64).contiguous()
+        if X is None:
+            if dtype != "identity":
+                raise ValueError('X = None needs dtype="identity"')
+            self.n = self.p = int(y.shape[0])
+            self.dtype = FLR_IDENTITY
+            on_dev = y.is_cuda
+            dev = y.device
+            y = y.to(dtype=torch.float64).contiguous()
+            xptr, ldx = None, 0
+        else:
+            if X.dim() != 2:
+                raise ValueError("X must be 2-D (n x p)")
+            if X.stride(1) != 1:
+                X = X.contiguous()
+            self.n, self.p = int(X.shape[0]), int(X.shape[1])
+            self.dtype = _dtype_code(X, dtype)
+            on_dev = X.is_cuda
+            dev = X.device
+            y = y.to(device=X.device, dtype=torch.float64).contiguous()
+            xptr, ldx = X.data_ptr(), X.stride(0)
         keep = [X, y]
         g = _graph(graph, self.p, keep)
         if g.kind == FLR_E_EDGES and on_dev and g.m:
-            keep[-1] = keep[-1].to(X.device)
+            keep[-1] = keep[-1].to(dev)
             g.edges = keep[-1].data_ptr()
-        self.device = X.device if on_dev else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev if on_dev else torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
         self.stream = stream
         h = ctypes.c_void_p()
-        st = lib.flr_create(X.data_ptr(), self.dtype, self.n, self.p, X.stride(0), y.data_ptr(),
+        st = lib.flr_create(xptr, self.dtype, self.n, self.p, ldx, y.data_ptr(),
                             ctypes.byref(g), FLR_MEM_DEVICE if on_dev else FLR_MEM_HOST,
                             ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
         if st != FLR_OK:

@@ -38,6 +38,11 @@ __global__ void transpose_kernel(const T* __restrict__ X, long long n, long long
   }
 }
 
+__global__ void fill_kernel(double* a, long long n, double v) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
 template <typename TX> __device__ __forceinline__ double widen(TX v);
 template <> __device__ __forceinline__ double widen<double>(double v) { return v; }
 template <> __device__ __forceinline__ double widen<float>(float v) { return (double)v; }
@@ -253,6 +258,11 @@ flr_status launch_solve_t(flr_handle* h, SolveParams& P, int G, size_t smem) {
   FLR_TRY(max_dynamic_smem((const void*)kern, h->device, &dyn_max));
   if (smem > (size_t)dyn_max) return FLR_ENOTIMPL;
   FLR_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+  // leading slab columns resident in shared memory (x_smem = 0), the rest streamed
+  if (P.ws != 0) {
+    P.ws = resident_columns(P.w, P.ldn, sizeof(TX), smem, dyn_max);
+    if (P.ws > 0) smem = (smem + 15) / 16 * 16 + (size_t)P.ws * (size_t)P.ldn * sizeof(TX);
+  }
   int nb = 0;
   FLR_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem));
   if (nb < 1 || G > nb * h->sm_count) return FLR_ENOTIMPL;
@@ -273,6 +283,8 @@ flr_status launch_solve(flr_handle* h, SolveParams& P, int G, size_t smem) {
                              : launch_solve_t<__nv_bfloat16, GK_STENCIL>(h, P, G, smem);
     case FLR_F16: return gk ? launch_solve_t<__half, GK_CSR>(h, P, G, smem)
                             : launch_solve_t<__half, GK_STENCIL>(h, P, G, smem);
+    case FLR_IDENTITY: return gk ? launch_solve_t<IdX, GK_CSR>(h, P, G, smem)
+                                 : launch_solve_t<IdX, GK_STENCIL>(h, P, G, smem);
   }
   return FLR_EINVAL;
 }
@@ -350,6 +362,7 @@ flr_status batch_group(flr_handle* h, int K, const double* l1, const double* l2,
     if (pc == FLR_PC_AUTO) pc = FLR_PC_TRIDIAG;
     P.precond = pc == FLR_PC_TRIDIAG ? PC_TRIDIAG : pc == FLR_PC_PAPER ? PC_PAPER : PC_JACOBI;
   }
+  P.max_refine = o.max_refine;
   P.Ps = h->Ps; P.Us = h->Us; P.Upart = h->Upart; P.U0part = h->U0part; P.U0 = h->U0;
   P.red = h->bred;
   P.bar = reinterpret_cast<unsigned*>(h->bctl);
@@ -414,7 +427,7 @@ flr_status batch_group(flr_handle* h, int K, const double* l1, const double* l2,
       stats[k].rel_change = hs[k].rel_change;
       stats[k].cg_relres = hs[k].cg_relres;
       stats[k].ms = ms;
-      stats[k].refine_steps = 0;
+      stats[k].refine_steps = hs[k].refine_steps;
       stats[k].reserved = 0;
       DevStats ds{};
       ds.f = hs[k].f;
@@ -467,8 +480,9 @@ flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_
                       flr_t* out) {
   if (!out) return FLR_EINVAL;
   *out = nullptr;
-  if (!X || !y || !E || n < 1 || p < 1 || ldx < p) return FLR_EINVAL;
-  if (dtype_size(dtype) == 0) return FLR_EINVAL;
+  const bool ident = dtype == FLR_IDENTITY;
+  if (!y || !E || n < 1 || p < 1) return FLR_EINVAL;
+  if (ident ? (X != nullptr || n != p) : (!X || ldx < p || dtype_size(dtype) == 0)) return FLR_EINVAL;
   if (mem != FLR_MEM_DEVICE && mem != FLR_MEM_HOST) return FLR_EINVAL;
   if (p >= (int64_t)INT32_MAX || n >= (int64_t)INT32_MAX) return FLR_ENOTIMPL;
   long long q1 = 1, q2 = p, m = 0;
@@ -493,9 +507,9 @@ flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_
   h->dtype = dtype;
   h->n = n; h->p = p; h->m = m;
   h->gkind = E->kind; h->q1 = q1; h->q2 = q2;
-  const size_t es = dtype_size(dtype);
+  const size_t es = ident ? 8 : dtype_size(dtype);
   const long long vec = 16 / (long long)es;
-  h->ldn = (n + vec - 1) / vec * vec;
+  h->ldn = ident ? vec : (n + vec - 1) / vec * vec;   // X = I keeps no n-vector accumulators
   flr_status s = FLR_OK;
   auto fail = [&](flr_status st) { release(h); return st; };
 
@@ -515,7 +529,9 @@ flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_
   }
   // buffers
   const size_t P = (size_t)p;
-  if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->Xt), (size_t)(p * h->ldn) * es)) != FLR_OK) return fail(s);
+  if (!ident &&
+      (s = dalloc(h, reinterpret_cast<unsigned char**>(&h->Xt), (size_t)(p * h->ldn) * es)) != FLR_OK)
+    return fail(s);
   if ((s = dalloc(h, &h->y, (size_t)n)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, &h->c, P)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, &h->d, P)) != FLR_OK) return fail(s);
@@ -536,6 +552,24 @@ flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_
   if ((s = dalloc(h, &h->ctl, 256)) != FLR_OK) return fail(s);
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) return fail(FLR_ECUDA);
 
+  if (ident) {   // X = I: X^T y = y, diag(X^T X) = 1
+    const cudaMemcpyKind kd = mem == FLR_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpyAsync(h->y, y, sizeof(double) * n, kd, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->c, y, sizeof(double) * n, kd, h->stream) != cudaSuccess)
+      return fail(FLR_ECUDA);
+    fill_kernel<<<(unsigned)std::min<long long>((p + 255) / 256, 1024), 256, 0, h->stream>>>(h->d, p, 1.0);
+    std::vector<double> yh((size_t)n);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(yh.data(), h->c, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return fail(FLR_ECUDA);
+    double s2 = 0.0;
+    for (double v : yh) s2 += v * v;
+    h->cnorm = std::sqrt(s2);
+    if (!std::isfinite(h->cnorm)) return fail(FLR_ENONFINITE);
+    *out = h;
+    return FLR_OK;
+  }
   // X -> column-major copy (padding rows are zero), y, then X^T y and diag(X^T X)
   if (cudaMemsetAsync(h->Xt, 0, (size_t)(p * h->ldn) * es, h->stream) != cudaSuccess) return fail(FLR_ECUDA);
   const void* Xdev = X;
@@ -590,7 +624,8 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   flr_default_opts(&o);
   if (opts) o = *opts;
   if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0 ||
-      o.max_refine < 0)
+      o.max_refine < 0 || (o.x_smem != 0 && o.x_smem != -1) ||
+      !(o.tol_cg_rel >= 0.0))
     return FLR_EINVAL;
   DeviceGuard dg(h->device);
 
@@ -602,8 +637,9 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   if ((precond == FLR_PC_TRIDIAG || precond == FLR_PC_PAPER) && h->gkind == FLR_E_EDGES) return FLR_ENOTIMPL;
 
   // grid: one block per SM at most; fewer for small problems
-  const long long work = h->n * h->p;
-  const long long per_block = h->dtype == FLR_F64 ? 8192 : 65536;
+  const bool ident = h->dtype == FLR_IDENTITY;
+  const long long work = ident ? h->p : h->n * h->p;
+  const long long per_block = ident ? 256 : h->dtype == FLR_F64 ? 8192 : 65536;
   long long G = o.grid > 0 ? o.grid : (work + per_block - 1) / per_block;
   G = std::max<long long>(1, std::min<long long>({G, (long long)h->sm_count, (long long)kMaxGrid, h->p}));
   long long w = (h->p + G - 1) / G;
@@ -612,8 +648,9 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   int levels = 0;
   while ((1LL << levels) < w) ++levels;
   const long long wpad = (w + 3) / 4 * 4;
-  const int V = (int)(16 / dtype_size(h->dtype));
-  const size_t smem = solve_smem_bytes(h->ldn, wpad, V);
+  const int V = ident ? XT<IdX>::V : (int)(16 / dtype_size(h->dtype));
+  const long long q2p = h->gkind == FLR_E_LATTICE ? h->q2 : h->p;
+  const size_t smem = solve_smem_bytes(h->ldn, wpad, V, halo_entries(wpad, q2p, h->p));
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
@@ -641,8 +678,10 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   P.rowptr = h->rowptr; P.col = h->col;
   P.lam1 = lambda1; P.lam2 = lambda2; P.eps = eps; P.tol = tol;
   P.tol_cg = o.tol_cg > 0.0 ? o.tol_cg : tol;
+  P.tol_cg_rel = o.tol_cg_rel;
   P.max_mm = o.max_mm; P.max_cg = o.max_cg; P.min_cg = o.min_cg; P.precond = precond;
   P.max_refine = o.max_refine;
+  P.ws = (o.x_smem == 0 && !ident) ? 1 : 0;   // 1: size the resident columns at launch
   P.w = w; P.wpad = wpad; P.levels = levels;
   P.beta_init = binit;
   P.x = h->x; P.z = h->z; P.pb0 = h->pb0; P.pb1 = h->pb1; P.wc = h->wc;

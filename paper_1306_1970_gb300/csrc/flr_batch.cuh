@@ -33,7 +33,7 @@ constexpr int kSlices = 3;               // BF16 slices per FP64/FP32 operand
 constexpr int kRedSlots = 3;
 
 struct BatchStats {
-  int mm_iters, cg_iters, status, pad;
+  int mm_iters, cg_iters, status, refine_steps;
   double f, f_eps, rel_change, cg_relres;
   double rel_prev;             // the relative change of f one MM iteration earlier
 };
@@ -52,6 +52,7 @@ struct BatchParams {
   double eps, tol, tol_cg;
   int max_mm, max_cg, min_cg;
   int precond;                 // PC_JACOBI, PC_TRIDIAG or PC_PAPER
+  int max_refine;              // FP64 residual restarts of each RHS's inner solve per MM iteration
   int S;                       // split-K chunks per row tile in phase A
   long long kchunk;            // columns per split-K chunk (multiple of 64)
   // per-RHS FP64 state, layout [k][j]
@@ -310,6 +311,10 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
   int* s_mm = s_act + 2 * kNRMax;
   int* s_cg = s_act + 3 * kNRMax;
   int* s_st = s_act + 4 * kNRMax;
+  int* s_rfn = s_act + 5 * kNRMax;                                 // in this refinement round
+  int* s_nref = s_act + 6 * kNRMax;                                // refinement rounds, this MM iteration
+  int* s_nreft = s_act + 7 * kNRMax;                               // refinement rounds, whole solve
+  int* s_cgr = s_act + 8 * kNRMax;                                 // CG iterations, this round
   uint64_t* mbar = reinterpret_cast<uint64_t*>(scal + 32 * kNRMax);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kNS);
 
@@ -350,6 +355,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
     }
   for (int k = tid; k < kNRMax; k += kBT) {
     s_act[k] = k < K ? 1 : 0; s_cga[k] = 0; s_mm[k] = 0; s_cg[k] = 0; s_st[k] = 0;
+    s_rfn[k] = 0; s_nref[k] = 0; s_nreft[k] = 0; s_cgr[k] = 0;
     s_f[k] = 0.0; s_fp[k] = 0.0; s_rel[k] = 0.0; s_relres[k] = 0.0; s_relp[k] = 0.0;
   }
   bool alive = gb.sync();
@@ -403,8 +409,34 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         if (tid < K && s_act[tid])
           tile_factor(P, tid, t * kTM, (int)(p - t * kTM < kTM ? p - t * kTM : kTM));
     }
-    // ---------------- objective and outer stop.  u0 = X b and X^T X b are
-    // recomputed exactly in FP64 on the CUDA cores every MM iteration.
+    // ---------------- rounds: first the objective, the outer stop test and the
+    // FP64 residual of the new surrogate; then, with max_refine > 0, refinement
+    // rounds for the RHS whose CG ran: the true FP64 residual of the same
+    // surrogate, and CG restarts from it while it is above tol_cg.
+    bool refining = false, finished = false;
+    for (int k = tid; k < kNRMax; k += kBT) s_nref[k] = 0;
+    __syncthreads();
+    while (true) {
+    const int* set = refining ? s_rfn : s_act;
+    if (refining) {   // S x with this MM iteration's weights (P.q held S p during CG)
+      for (long long t = b; t < ntiles; t += G)
+        for (int e = tid; e < K * kTM; e += kBT) {
+          const int k = e / kTM;
+          const long long j = t * kTM + (e % kTM);
+          if (!set[k] || j >= p) continue;
+          const double* xk = P.x + (long long)k * p;
+          const long long o = (long long)k * p + j, col = j % q2;
+          const double xj = ldcg(xk + j);
+          double lap = 0.0;
+          if (col != 0) lap = fma(P.wl[o], xj - ldcg(xk + j - 1), lap);
+          if (col != q2 - 1 && j + 1 < p) lap = fma(P.wr[o], xj - ldcg(xk + j + 1), lap);
+          if (j >= q2) lap = fma(P.wu[o], xj - ldcg(xk + j - q2), lap);
+          if (j + q2 < p) lap = fma(P.wd[o], xj - ldcg(xk + j + q2), lap);
+          P.q[o] = fma(P.la[o], xj, lap);
+        }
+      __syncthreads();
+    }
+    // u0 = X b and X^T X b recomputed exactly in FP64 on the CUDA cores
     {
       // FP64 refinement pass 1: U0 = X b (CUDA cores, FP64)
       for (long long it = b; it < mtiles * P.S; it += G) {
@@ -420,7 +452,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
           for (int e = tid; e < 64 * kNRMax; e += kBT) {
             const int jj = e / kNRMax, k = e % kNRMax;
             const long long j = j0 + jj;
-            b64[jj * kNRMax + k] = (k < K && s_act[k] && j < je) ? ldcg(P.x + (long long)k * p + j) : 0.0;
+            b64[jj * kNRMax + k] = (k < K && set[k] && j < je) ? ldcg(P.x + (long long)k * p + j) : 0.0;
           }
           __syncthreads();
           const int jn = (int)(je - j0 < 64 ? je - j0 : 64);
@@ -442,7 +474,9 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         }
       }
       __syncthreads();
-      if (!grid_red(s_pen, s_pen, 2 * kNRMax)) { alive = false; break; }
+      if (!refining) {
+        if (!grid_red(s_pen, s_pen, 2 * kNRMax)) { alive = false; break; }
+      } else if (!gb.sync()) { alive = false; break; }
       // U0 = sum of the split partials, and the residual sum of squares
       for (int f = tid; f < kNRMax; f += kBT) s_rss[f] = 0.0;
       __syncthreads();
@@ -452,7 +486,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         for (long long e = tid; e < (long long)K * (i1 > i0 ? i1 - i0 : 0); e += kBT) {
           const int k = (int)(e / (i1 - i0));
           const long long i = i0 + e % (i1 - i0);
-          if (!s_act[k]) continue;
+          if (!set[k]) continue;
           double sv = 0.0;
           for (int sp = 0; sp < P.S; ++sp) sv += ldcg(P.U0part + ((long long)sp * NR + k) * n + i);
           P.U0[(long long)k * n + i] = sv;
@@ -461,8 +495,11 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         }
       }
       __syncthreads();
-      if (!grid_red(s_rss, s_rss, kNRMax)) { alive = false; break; }
+      if (!refining) {
+        if (!grid_red(s_rss, s_rss, kNRMax)) { alive = false; break; }
+      } else if (!gb.sync()) { alive = false; break; }
     }
+    if (!refining) {
     if (tid < K) {
       const int k = tid;
       if (s_act[k]) {
@@ -480,7 +517,8 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
     __syncthreads();
     int nact = 0;
     for (int k = 0; k < K; ++k) nact += s_act[k];
-    if (nact == 0) break;
+    if (nact == 0) { finished = true; break; }
+    }
     // ---------------- FP64 refinement pass 2: r0 = c - X^T U0 - S b; z0; p1 = z0
     for (int f = tid; f < kNRMax; f += kBT) { s_rz[f] = 0.0; s_rr[f] = 0.0; }
     __syncthreads();
@@ -495,7 +533,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         for (int e = tid; e < 64 * kNRMax; e += kBT) {
           const int ii = e / kNRMax, k = e % kNRMax;
           const long long i = i0 + ii;
-          b64[ii * kNRMax + k] = (k < K && s_act[k] && i < n) ? ldcg(P.U0 + (long long)k * n + i) : 0.0;
+          b64[ii * kNRMax + k] = (k < K && set[k] && i < n) ? ldcg(P.U0 + (long long)k * n + i) : 0.0;
         }
         __syncthreads();
         const int in = (int)(n - i0 < 64 ? n - i0 : 64);
@@ -512,7 +550,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
 #pragma unroll
         for (int m = 0; m < 32; ++m) {
           const int k = h * 32 + m;
-          if (k < K && s_act[k]) P.t0[(long long)k * p + j] = acc[m];
+          if (k < K && set[k]) P.t0[(long long)k * p + j] = acc[m];
         }
       }
     }
@@ -523,7 +561,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         for (int e = tid; e < K * kTM; e += kBT) {
           const int k = e / kTM;
           const long long j = t * kTM + (e % kTM);
-          if (!s_act[k]) continue;                  // warp-uniform
+          if (!set[k]) continue;                    // warp-uniform
           double v_rz = 0.0, v_rr = 0.0;
           if (j < p) {
             const long long o = (long long)k * p + j;
@@ -543,7 +581,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
           __syncthreads();
           const int len = (int)(p - t * kTM < kTM ? p - t * kTM : kTM);
           for (int k = tid >> 5; k < K; k += kBT / 32)   // one warp per RHS
-            if (s_act[k]) {
+            if (set[k]) {
               const double rz = tile_solve_warp(P, k, t * kTM, len, pc);
               if ((tid & 31) == 0) atomicAdd(&s_rz[k], rz);
             }
@@ -560,7 +598,19 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       if (!grid_red(tmp, tmp, 2 * kNRMax)) { alive = false; break; }
       for (int f = tid; f < kNRMax; f += kBT) { s_rz[f] = tmp[f]; s_rr[f] = tmp[kNRMax + f]; s_gam[f] = 0.0; }
     }
-    if (tid < kNRMax) s_cga[tid] = (tid < K && s_act[tid]) ? 1 : 0;
+    if (tid < kNRMax) {
+      const int k = tid;
+      int go = (k < K && set[k] && s_act[k]) ? 1 : 0;
+      if (refining && go) {   // the true residual decides whether CG restarts
+        ++s_nref[k];
+        ++s_nreft[k];
+        const double rel_r = sqrt(s_rr[k]) / P.cnorm;
+        s_relres[k] = rel_r;
+        if (rel_r <= P.tol_cg) go = 0;
+      }
+      s_cga[k] = go;
+      s_cgr[k] = 0;
+    }
     __syncthreads();
     // ---------------- CG iterations for all active RHS
     int kcg = 0;
@@ -571,7 +621,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
           const double rel_r = sqrt(s_rr[k]) / P.cnorm;
           s_relres[k] = rel_r;
           if (kcg >= P.max_cg || (kcg >= P.min_cg && rel_r <= P.tol_cg)) s_cga[k] = 0;
-          else s_cg[k] += 1;
+          else { s_cg[k] += 1; s_cgr[k] += 1; }
         }
       }
       __syncthreads();
@@ -795,6 +845,20 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       __syncthreads();
     }
     if (!alive) break;
+    // the next refinement round: RHS whose CG ran in this round, with restarts left
+    if (tid < kNRMax) {
+      const int k = tid;
+      s_rfn[k] = (k < K && s_act[k] && s_cgr[k] > 0 && s_nref[k] < P.max_refine) ? 1 : 0;
+    }
+    __syncthreads();
+    int nrf = 0;
+    for (int k = 0; k < K; ++k) nrf += s_rfn[k];
+    if (nrf == 0) break;
+    refining = true;
+    }   // rounds
+    if (finished) break;
+
+    if (!alive) break;
     if (tid < K) {
       if (s_act[tid]) { s_fp[tid] = s_f[tid]; s_mm[tid] += 1; }
     }
@@ -810,7 +874,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       S->mm_iters = s_mm[k];
       S->cg_iters = s_cg[k];
       S->status = s_st[k];
-      S->pad = 0;
+      S->refine_steps = s_nreft[k];
       S->f = s_f[k];
       S->f_eps = 0.0;
       S->rel_change = s_rel[k];

@@ -8,7 +8,7 @@
 
 namespace flr {
 
-constexpr int kThreads = 512;            // threads per block of the solve kernel
+constexpr int kThreads = 256;            // threads per block of the solve kernel
 constexpr int kWarps = kThreads / 32;
 constexpr int kNF = 4;                   // scalar fields per grid-reduction slot
 constexpr int kMaxLevels = 13;           // PCR levels: block chunks up to 8192 indices
@@ -75,6 +75,14 @@ template <> struct XT<__half> {
       o[2 * i + 1] = f.y;
     }
   }
+};
+
+// X = I (the FLSA): no matrix is stored or read; the solve kernel replaces
+// every X product by the vector itself.  V and Acc only size shared buffers.
+struct IdX {};
+template <> struct XT<IdX> {
+  static constexpr int V = 2;
+  using Acc = double;
 };
 
 // Device-wide nanosecond timer (comparable across kernels on one GPU).

@@ -139,6 +139,10 @@ flr_status run(const SolveParams& P0, const void* Xt, const double* y, long long
   }
   const int dyn_max = optin - (int)fa.sharedSizeBytes;
   if (smem > (size_t)dyn_max) return FLR_ENOTIMPL;
+  if (P.ws != 0) {   // leading slab columns resident in shared memory
+    P.ws = resident_columns(P.w, P.ldn, sizeof(TX), smem, dyn_max);
+    if (P.ws > 0) smem = (smem + 15) / 16 * 16 + (size_t)P.ws * (size_t)P.ldn * sizeof(TX);
+  }
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess) {
     (void)cudaGetLastError();
     return FLR_ECUDA;
@@ -182,7 +186,8 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   flr_default_opts(&o);
   if (opts) o = *opts;
   if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0 ||
-      o.max_refine < 0)
+      o.max_refine < 0 || (o.x_smem != 0 && o.x_smem != -1) ||
+      !(o.tol_cg_rel >= 0.0))
     return FLR_EINVAL;
   int precond = o.precond;
   if (precond == FLR_PC_AUTO) precond = FLR_PC_TWOLEVEL;
@@ -208,7 +213,7 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   int levels = 0;
   while ((1LL << levels) < w) ++levels;
   const long long wpad = (w + 3) / 4 * 4;
-  const size_t smem = solve_smem_bytes(ldn, wpad, (int)(16 / es));
+  const size_t smem = solve_smem_bytes(ldn, wpad, (int)(16 / es), halo_entries(wpad, q2, p));
 
   // ---- scratch layout inside the static array
   const size_t vecb = up256(sizeof(double) * (size_t)p);
@@ -250,8 +255,10 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   P.rowptr = nullptr; P.col = nullptr;
   P.lam1 = lambda1; P.lam2 = lambda2; P.eps = eps; P.tol = tol;
   P.tol_cg = o.tol_cg > 0.0 ? o.tol_cg : tol;
+  P.tol_cg_rel = o.tol_cg_rel;
   P.max_mm = o.max_mm; P.max_cg = o.max_cg; P.min_cg = o.min_cg; P.precond = precond;
   P.max_refine = o.max_refine;
+  P.ws = o.x_smem == 0 ? 1 : 0;
   P.w = w; P.wpad = wpad; P.levels = levels;
   P.beta_init = nullptr;
   P.x = vec[0]; P.z = vec[1]; P.pb0 = vec[2]; P.pb1 = vec[3];

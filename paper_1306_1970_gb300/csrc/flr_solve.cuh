@@ -60,6 +60,7 @@
 // and block reductions go through shared memory and a single warp.
 #pragma once
 #include <cmath>
+#include <type_traits>
 
 #include "flr_device.cuh"
 
@@ -85,7 +86,8 @@ enum NbrBits : unsigned char {
 constexpr unsigned char NB_STRONG = NB_SL | NB_SR | NB_SU | NB_SD;
 constexpr double kStrong = 16.0;   // strong-edge threshold of PC_TWOLEVEL
 
-constexpr int kRF = 2;   // fields per block reduction
+constexpr int kRF = 3;   // fields per block reduction
+constexpr int kLA = 16;  // 16-byte X loads in flight per thread in phase A
 constexpr int kUR = 1;   // replicas of each u accumulator: block b adds into replica b % kUR,
                          // spreading the atomics of X p over kUR times more L2 lines
 
@@ -100,8 +102,10 @@ struct SolveParams {
   const long long* rowptr;   // CSR (both orientations of every edge)
   const int* col;
   double lam1, lam2, eps, tol, tol_cg;
+  double tol_cg_rel;         // adaptive inner tolerance factor (0 = off)
   int max_mm, max_cg, min_cg, precond;
   int max_refine;            // FP64 residual restarts of the inner solve per MM iteration
+  int ws;                    // leading columns of a block's slab kept in shared memory
   long long w, wpad;         // coefficients per block, padded to a multiple of 4
   int levels;                // PCR levels for the block chunk
   const double* beta_init;   // nullptr -> X_j^T y / X_j^T X_j
@@ -144,11 +148,30 @@ inline double estimated_error(const DevStats& s) {
   return e + tail;
 }
 
+// Remote stencil neighbours of a block of w consecutive coefficients: the left
+// one, the right one, and on a lattice (row length q2 < p) the min(w, q2)
+// vertical ones on each side.
+__host__ __device__ inline long long halo_entries(long long w, long long q2, long long p) {
+  return 2 + (q2 < p ? 2 * (w < q2 ? w : q2) : 0);
+}
+
+// Columns of a block's X slab that stay in shared memory for the whole solve:
+// as many of its w columns (ldn elements of es bytes each) as fit next to the
+// kernel's other shared memory (`base` bytes, rounded up to 16) within dyn_max.
+inline int resident_columns(long long w, long long ldn, size_t es, size_t base, int dyn_max) {
+  const long long room = (long long)dyn_max - (long long)((base + 15) / 16 * 16);
+  if (room <= 0) return 0;
+  long long c = room / (ldn * (long long)es);
+  return (int)(c < w ? c : w);
+}
+
 // shared-memory bytes of mm_solve_kernel (the host uses the same formula)
-__host__ __device__ inline size_t solve_smem_bytes(long long ldn, long long wpad, int V) {
+__host__ __device__ inline size_t solve_smem_bytes(long long ldn, long long wpad, int V, long long nh) {
   return (size_t)ldn * 8 + (size_t)wpad * 8 + (size_t)kThreads * V * 8 + (size_t)wpad * 8 +
          6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 +
-         ((size_t)kRF * kThreads + 16) * 8 + (size_t)wpad * 4 + (size_t)wpad;
+         ((size_t)kRF * kThreads + 16) * 8 +
+         2 * (size_t)nh * 8 + (size_t)nh * 4 +            // halo p values, 1/q_c, component ids
+         (size_t)wpad * 4 + (size_t)wpad;
 }
 
 template <typename TX, typename A>
@@ -184,10 +207,25 @@ __device__ __forceinline__ void block_reduce(double (&v)[F], double* rs, int nac
   for (int f = 0; f < F; ++f) v[f] = rs[kRF * kThreads + f];
 }
 
+// 16 bytes of column jj (block-relative) at element offset `off`: from the
+// shared-memory copy for the first ws columns, else streamed from global memory.
+__device__ __forceinline__ uint4 lds16(uint32_t a) {
+  uint4 r;
+  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "r"(a));
+  return r;
+}
+template <typename TX>
+__device__ __forceinline__ uint4 ldx(const TX* __restrict__ Xt, uint32_t xs, int ws, long long ldn,
+                                     long long j0, int jj, long long off) {
+  if (jj < ws) return lds16(xs + (uint32_t)(((long long)jj * ldn + off) * (long long)sizeof(TX)));
+  return ld_stream16(Xt + (j0 + jj) * ldn + off);
+}
+
 // u[0:n] += sum_{j in slab} X[:, j] * v[j - j0]   (v staged in shared memory)
 template <typename TX, typename A>
-__device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restrict__ Xt,
+__device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restrict__ Xt, uint32_t xs,
                                         long long j0, int wl, const A* vs, A* red, A* u) {
+  const int ws = P.ws;
   constexpr int V = XT<TX>::V;
   const int tid = threadIdx.x;
   const int nv = (int)(P.ldn / V);
@@ -197,14 +235,14 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
       A acc[V];
 #pragma unroll
       for (int e = 0; e < V; ++e) acc[e] = A(0);
-      const TX* base = Xt + j0 * P.ldn + (long long)rv * V;
+      const long long off = (long long)rv * V;
       int j = 0;
-      for (; j + 8 <= wl; j += 8) {
-        uint4 raw[8];
+      for (; j + kLA <= wl; j += kLA) {
+        uint4 raw[kLA];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) raw[k] = ld_stream16(base + (long long)(j + k) * P.ldn);
+        for (int k = 0; k < kLA; ++k) raw[k] = ldx<TX>(Xt, xs, ws, P.ldn, j0, j + k, off);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < kLA; ++k) {
           A xv[V];
           cvt_to<TX, A>(raw[k], xv);
           const A s = vs[j + k];
@@ -214,7 +252,7 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
       }
       for (; j < wl; ++j) {
         A xv[V];
-        cvt_to<TX, A>(ld_stream16(base + (long long)j * P.ldn), xv);
+        cvt_to<TX, A>(ldx<TX>(Xt, xs, ws, P.ldn, j0, j, off), xv);
         const A s = vs[j];
 #pragma unroll
         for (int e = 0; e < V; ++e) acc[e] = fma(xv[e], s, acc[e]);
@@ -232,14 +270,14 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
 #pragma unroll
     for (int e = 0; e < V; ++e) acc[e] = A(0);
     if (cg < ncg) {
-      const TX* base = Xt + j0 * P.ldn + (long long)rv * V;
+      const long long off = (long long)rv * V;
       int j = cg;
-      for (; j + 7 * ncg < wl; j += 8 * ncg) {
-        uint4 raw[8];
+      for (; j + (kLA - 1) * ncg < wl; j += kLA * ncg) {
+        uint4 raw[kLA];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) raw[k] = ld_stream16(base + (long long)(j + k * ncg) * P.ldn);
+        for (int k = 0; k < kLA; ++k) raw[k] = ldx<TX>(Xt, xs, ws, P.ldn, j0, j + k * ncg, off);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < kLA; ++k) {
           A xv[V];
           cvt_to<TX, A>(raw[k], xv);
           const A s = vs[j + k * ncg];
@@ -249,7 +287,7 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
       }
       for (; j < wl; j += ncg) {
         A xv[V];
-        cvt_to<TX, A>(ld_stream16(base + (long long)j * P.ldn), xv);
+        cvt_to<TX, A>(ldx<TX>(Xt, xs, ws, P.ldn, j0, j, off), xv);
         const A s = vs[j];
 #pragma unroll
         for (int e = 0; e < V; ++e) acc[e] = fma(xv[e], s, acc[e]);
@@ -271,8 +309,9 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
 // tv[jj] = X[:, j0+jj]^T u  for jj in [0, wl)   (u staged in shared memory).
 // One warp per pair of columns; each lane keeps CPW x UR 16-byte loads in flight.
 template <typename TX, typename A>
-__device__ __forceinline__ void phase_c(const SolveParams& P, const TX* __restrict__ Xt,
+__device__ __forceinline__ void phase_c(const SolveParams& P, const TX* __restrict__ Xt, uint32_t xs,
                                         long long j0, int wl, const A* us, double* tv) {
+  const int ws = P.ws;
   constexpr int V = XT<TX>::V;
   constexpr int CPW = 2;  // columns per warp
   constexpr int UR = 4;   // row vectors per lane per round
@@ -290,7 +329,7 @@ __device__ __forceinline__ void phase_c(const SolveParams& P, const TX* __restri
         for (int u = 0; u < UR; ++u) {
           const int rv = rv0 + 32 * u;
           if (base + c < wl && rv < nv)
-            raw[c][u] = ld_stream16(Xt + (j0 + base + c) * P.ldn + (long long)rv * V);
+            raw[c][u] = ldx<TX>(Xt, xs, ws, P.ldn, j0, base + c, (long long)rv * V);
         }
 #pragma unroll
       for (int u = 0; u < UR; ++u) {
@@ -502,6 +541,8 @@ template <typename TX, int GK>
 __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams P) {
   using Acc = typename XT<TX>::Acc;
   constexpr int V = XT<TX>::V;
+  // X = I: n = p, X^T y = y, X^T X = I; the X products become the vector itself
+  constexpr bool IDX = std::is_same<TX, IdX>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int tid = threadIdx.x;
   const int G = gridDim.x, b = blockIdx.x;
@@ -521,8 +562,24 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   double* cst = pw + 6 * wp;                                // 6*wpad: per-column constants
   double* own = cst + 6 * wp;                               // 6*wpad: own CG vectors
   double* rs = own + 6 * wp;                                // kRF*kThreads + 16
-  int* cid_s = reinterpret_cast<int*>(rs + kRF * kThreads + 16);                  // wpad
-  unsigned char* nb = reinterpret_cast<unsigned char*>(cid_s + wp);               // wpad
+  const long long nh = halo_entries(wp, q2, p);
+  double* hv = rs + kRF * kThreads + 16;                    // nh: p at the remote neighbours
+  double* hq = hv + nh;                                     // nh: their 1/q_c
+  int* cid_s = reinterpret_cast<int*>(hq + nh);                                   // wpad
+  int* hc = cid_s + wp;                                                           // nh
+  unsigned char* nb = reinterpret_cast<unsigned char*>(hc + nh);                  // wpad
+  // ws leading columns of the slab, resident for the whole solve (16-byte aligned)
+  const size_t xs_off = (solve_smem_bytes(P.ldn, wp, V, nh) + 15) / 16 * 16;
+  const uint32_t xs_sh = (uint32_t)__cvta_generic_to_shared(smraw) + (uint32_t)xs_off;
+  // The component sums of r of the last CG iteration, copied to shared memory
+  // after its barrier 2 when nc <= kThreads * V; they share the phase A partials'
+  // space, which holds nothing between phase A and the next iteration's.
+  double* scs = redd;
+  const int sc_cap = kThreads * V;
+  // remote halo: slot 0 the left neighbour of the first owned coefficient, 1 the
+  // right neighbour of the last, then hn up and hn down neighbours (lattice)
+  const int hn = (q2 < p) ? (int)(wl < q2 ? wl : q2) : 0;
+  const int hd0 = (wl > q2) ? (int)(wl - q2) : 0;           // first jj whose down neighbour is remote
   double* s_la = cst;            // lam1 a_j
   double* s_wl = cst + wp;       // lam2 w(j-1, j) etc.
   double* s_wr = cst + 2 * wp;
@@ -576,6 +633,14 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
                    (P.precond == PC_TRIDIAG || P.precond == PC_PAPER || (two && P.q2 >= P.p));
   const int lane = tid & 31, warp = tid >> 5;
 
+  // ---- the shared-memory copy of the slab's first ws columns
+  if constexpr (!IDX) {
+    const int wsl = P.ws < wl ? P.ws : wl;   // the last block may own fewer columns
+    const long long nvec = (long long)wsl * P.ldn * (long long)sizeof(TX) / 16;
+    const uint4* src = reinterpret_cast<const uint4*>(Xt + j0 * P.ldn);
+    uint4* dst = reinterpret_cast<uint4*>(smraw + xs_off);
+    for (long long v = tid; v < nvec; v += kThreads) dst[v] = __ldg(src + v);
+  }
   // ---- initialisation (Algorithm 1): beta_j = X_j^T y / X_j^T X_j
   for (int jj = tid; jj < wl; jj += kThreads) {
     const long long j = j0 + jj;
@@ -671,19 +736,31 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
     __syncthreads();
     if (tri) setup_tridiag(P, j0, wl, tv, s_wl, s_wr, pw);
     // ---------------- u0 = X x in FP64 (refinement pass)
-    zero_u(U1);
-    if (!u0_ready)
-      phase_a<TX, double>(P, Xt, j0, wl, vsd, redd, reinterpret_cast<double*>(U0) + (long long)rep * P.ldn);
+    double pr3[3] = {pen[0], pen[1], 0.0};   // penalties, and ||y - x||^2 when X = I
+    if constexpr (!IDX) {
+      zero_u(U1);
+      if (!u0_ready)
+        phase_a<TX, double>(P, Xt, xs_sh, j0, wl, vsd, redd, reinterpret_cast<double*>(U0) + (long long)rep * P.ldn);
+    } else {
+      for (int jj = tid; jj < wl; jj += kThreads) {
+        const double d = P.y[j0 + jj] - xs[jj];
+        pr3[2] = fma(d, d, pr3[2]);
+      }
+    }
     u0_ready = false;
-    block_reduce<2>(pen, rs, ncol);
-    if (!grid_sum(pen)) return;
+    block_reduce<3>(pr3, rs, ncol);
+    if (!grid_sum(pr3)) return;
+    pen[0] = pr3[0];
+    pen[1] = pr3[1];
     // ---------------- f(beta(r)) (Eq. obj) and the outer stop test
-    {
+    if constexpr (!IDX) {
       double rv[1] = {stage_u<double>(reinterpret_cast<const double*>(U0), usd, n, P.ldn, P.y, true)};
       block_reduce<1>(rv, rs, kThreads);
       rss_last = rv[0];
-      f = 0.5 * rv[0] + P.lam1 * pen[0] + P.lam2 * pen[1];
+    } else {
+      rss_last = pr3[2];
     }
+    f = 0.5 * rss_last + P.lam1 * pen[0] + P.lam2 * pen[1];
     if (!isfinite(f)) { status = ST_NONFINITE; break; }
     if (mm > 0) {
       rel_prev = rel;
@@ -691,8 +768,11 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       if (rel <= P.tol) break;
     }
     if (mm >= P.max_mm) { status = ST_NOTCONV; break; }
+    // inner tolerance of this MM iteration
+    const double tol_in = fmax(P.tol_cg, P.tol_cg_rel * (mm > 0 ? rel : 1.0));
     // ---------------- r0 = c - Q x0 (FP64), z0 = M^-1 r0, p1 = z0 (Algorithm 2)
-    phase_c<TX, double>(P, Xt, j0, wl, usd, tv);
+    if constexpr (!IDX) phase_c<TX, double>(P, Xt, xs_sh, j0, wl, usd, tv);
+    else for (int jj = tid; jj < wl; jj += kThreads) tv[jj] = xs[jj];
     for (int jj = tid; jj < wl; jj += kThreads) rsm[jj] = (P.c[j0 + jj] - tv[jj]) - qs[jj];
     __syncthreads();
     int nc = 0;   // coarse components of this MM iteration (PC_TWOLEVEL)
@@ -817,7 +897,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
         if (tid == 0) {
           const double rel_r = sqrt(rr) / P.cnorm;
           sc[0] = rel_r;
-          sc[1] = (k >= P.max_cg || (k >= P.min_cg && rel_r <= P.tol_cg)) ? 1.0 : 0.0;
+          sc[1] = (k >= P.max_cg || (k >= P.min_cg && rel_r <= tol_in)) ? 1.0 : 0.0;
         }
         __syncthreads();
         relres = sc[0];
@@ -841,17 +921,51 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
           }
           return fma(gamma, ldcg(po + kk), zk);
         };
-        double sv[1] = {0.0};
+        // component sums of the previous iteration: the shared-memory copy made
+        // after its barrier 2 when they fit, else global memory
+        const bool sc_smem = nc <= sc_cap;
+        if (GK == GK_STENCIL) {
+          // p at the block's remote neighbours, every load of the block in flight at
+          // once (z + coarse part + gamma p_old as in pval, or p itself at k = 0);
+          // 1/q_c and component ids of remote neighbours are fetched at k = 0 and
+          // kept for the rest of the MM iteration
+          for (int e = tid; e < 2 + 2 * hn; e += kThreads) {
+            long long kk;
+            unsigned char bit;
+            if (e == 0) { kk = j0 - 1; bit = NB_L; }
+            else if (e == 1) { kk = j1; bit = NB_R; }
+            else if (e < 2 + hn) { kk = j0 + (e - 2) - q2; bit = NB_U; }
+            else { kk = j0 + hd0 + (e - 2 - hn) + q2; bit = NB_D; }
+            const int jj = e == 0 ? 0 : e == 1 ? wl - 1 : e < 2 + hn ? e - 2 : hd0 + (e - 2 - hn);
+            if (wl == 0 || !(nb[jj] & bit)) continue;
+            double v;
+            if (k == 0) {
+              v = ldcg(pc + kk);
+              if (two) { hc[e] = __ldcg(P.cid + kk); hq[e] = ldcg(P.qcinv + kk); }
+            } else {
+              double zk = ldcg(P.z + kk);
+              const double pk = ldcg(po + kk);
+              if (two) {
+                const int c = hc[e];
+                if (c >= 0) zk = fma(sc_smem ? scs[c] : ldcg(Sold + c), hq[e], zk);
+              }
+              v = fma(gamma, pk, zk);
+            }
+            hv[e] = v;
+          }
+          __syncthreads();
+        }
+        double sv[2] = {0.0, 0.0};   // p^T S p, and ||p||^2 when X = I
         for (int jj = tid; jj < wl; jj += kThreads) {
           const long long j = j0 + jj;
           const double pj = ps[jj];
           double lap = 0.0;
           if (GK == GK_STENCIL) {
             const unsigned char fl = nb[jj];
-            const double pl = (fl & NB_L) ? pval(j - 1) : pj;
-            const double pr = (fl & NB_R) ? pval(j + 1) : pj;
-            const double pu = (fl & NB_U) ? pval(j - q2) : pj;
-            const double pd = (fl & NB_D) ? pval(j + q2) : pj;
+            const double pl = (fl & NB_L) ? (jj == 0 ? hv[0] : ps[jj - 1]) : pj;
+            const double pr = (fl & NB_R) ? (jj == wl - 1 ? hv[1] : ps[jj + 1]) : pj;
+            const double pu = (fl & NB_U) ? (jj < q2 ? hv[2 + jj] : ps[jj - q2]) : pj;
+            const double pd = (fl & NB_D) ? (jj >= hd0 ? hv[2 + hn + jj - hd0] : ps[jj + q2]) : pj;
             lap = fma(s_wl[jj], pj - pl, lap);
             lap = fma(s_wr[jj], pj - pr, lap);
             lap = fma(s_wu[jj], pj - pu, lap);
@@ -863,16 +977,26 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
           const double spj = fma(s_la[jj], pj, lap);
           qs[jj] = spj;
           sv[0] = fma(pj, spj, sv[0]);
+          if constexpr (IDX) sv[1] = fma(pj, pj, sv[1]);   // ||X p||^2 = ||p||^2
           vs[jj] = (Acc)pj;
         }
-        zero_u(Unext);
-        __syncthreads();
-        phase_a<TX, Acc>(P, Xt, j0, wl, vs, red, Ucur + (long long)rep * P.ldn * 8 / (long long)sizeof(Acc));
-        block_reduce<1>(sv, rs, ncol);
-        if (!grid_sum(sv)) return;
-        // p^T Q p = ||X p||^2 + p^T S p
-        double uu[1] = {stage_u<Acc>(Ucur, us, n, P.ldn, P.y, false)};
-        block_reduce<1>(uu, rs, kThreads);
+        double uu[1] = {0.0};
+        if constexpr (!IDX) {
+          zero_u(Unext);
+          __syncthreads();
+          phase_a<TX, Acc>(P, Xt, xs_sh, j0, wl, vs, red, Ucur + (long long)rep * P.ldn * 8 / (long long)sizeof(Acc));
+          double sv1[1] = {sv[0]};
+          block_reduce<1>(sv1, rs, ncol);
+          if (!grid_sum(sv1)) return;
+          sv[0] = sv1[0];
+          // p^T Q p = ||X p||^2 + p^T S p
+          uu[0] = stage_u<Acc>(Ucur, us, n, P.ldn, P.y, false);
+          block_reduce<1>(uu, rs, kThreads);
+        } else {
+          block_reduce<2>(sv, rs, ncol);
+          if (!grid_sum(sv)) return;
+          uu[0] = sv[1];
+        }
         if (tid == 0) {
           const double pq = uu[0] + sv[0];
           const bool bad = !(pq > 0.0) || !isfinite(pq);
@@ -882,7 +1006,8 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
         __syncthreads();
         if (sc[3] != 0.0) { status = (int)sc[3]; break; }
         const double nu = sc[2];
-        phase_c<TX, Acc>(P, Xt, j0, wl, us, tv);
+        if constexpr (!IDX) phase_c<TX, Acc>(P, Xt, xs_sh, j0, wl, us, tv);
+        else for (int jj = tid; jj < wl; jj += kThreads) tv[jj] = ps[jj];
         for (int jj = tid; jj < wl; jj += kThreads) {
           const double xn = fma(nu, ps[jj], xs[jj]);
           xs[jj] = xn;
@@ -917,6 +1042,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
               const int c = c0 + u * kThreads;
               sv_[u] = c < nc ? ldcg(Scur + c) : 0.0;
               qv_[u] = c < nc ? ldcg(P.qci + c) : 0.0;
+              if (c < nc && sc_smem) scs[c] = sv_[u];
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) cz[0] = fma(sv_[u] * sv_[u], qv_[u], cz[0]);
@@ -935,7 +1061,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
           double zj = zs[jj];
           if (two) {
             const int c = cid_s[jj];
-            if (c >= 0) zj = fma(ldcg(Scur + c), qi_s[jj], zj);
+            if (c >= 0) zj = fma(sc_smem ? scs[c] : ldcg(Scur + c), qi_s[jj], zj);
           }
           const double v = fma(gamma, ps[jj], zj);
           ps[jj] = v;
@@ -970,9 +1096,11 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
         qs[jj] = fma(s_la[jj], xj, lap);
         vsd[jj] = xj;
       }
-      zero_u(ucur ? P.ub0 : P.ub1);
-      __syncthreads();
-      phase_a<TX, double>(P, Xt, j0, wl, vsd, redd, reinterpret_cast<double*>(Ux) + (long long)rep * P.ldn);
+      if constexpr (!IDX) {
+        zero_u(ucur ? P.ub0 : P.ub1);
+        __syncthreads();
+        phase_a<TX, double>(P, Xt, xs_sh, j0, wl, vsd, redd, reinterpret_cast<double*>(Ux) + (long long)rep * P.ldn);
+      }
       if (!gb.sync()) return;
       // the last CG iteration's component sums are no longer read: clear them;
       // the other array was cleared during that iteration and takes 1_c^T r
@@ -980,9 +1108,14 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       double* Snew = ((k - 1 + kpar) & 1) ? P.sc1 : P.sc0;
       if (two)
         for (long long c = j0 + tid; c < j1 && c < nc; c += kThreads) Slast[c] = 0.0;
-      (void)stage_u<double>(reinterpret_cast<const double*>(Ux), usd, n, P.ldn, P.y, false);
-      __syncthreads();
-      phase_c<TX, double>(P, Xt, j0, wl, usd, tv);
+      if constexpr (!IDX) {
+        (void)stage_u<double>(reinterpret_cast<const double*>(Ux), usd, n, P.ldn, P.y, false);
+        __syncthreads();
+        phase_c<TX, double>(P, Xt, xs_sh, j0, wl, usd, tv);
+      } else {
+        for (int jj = tid; jj < wl; jj += kThreads) tv[jj] = xs[jj];
+        __syncthreads();
+      }
       double rr1[1] = {0.0};
       for (int jj = tid; jj < wl; jj += kThreads) {
         const double rj = (P.c[j0 + jj] - tv[jj]) - qs[jj];
@@ -1000,7 +1133,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       ++nref_mm;
       ++nref_total;
       relres = sqrt(rr1[0]) / P.cnorm;
-      if (relres <= P.tol_cg) {   // accurate: X x stays in accumulator `ucur` for the next MM iteration
+      if (relres <= tol_in) {   // accurate: X x stays in accumulator `ucur` for the next MM iteration
         u0_ready = true;
         break;
       }

@@ -29,6 +29,8 @@ from oracle import mm  # noqa: E402
 
 
 def fingerprint(pr):
+    if isinstance(pr, fi.DenoiseProblem):
+        return {"y_head": [float(v) for v in pr.y[:4]], "y_sum": float(pr.y.sum())}
     X = pr.X64()
     return {"x_sum": float(X.sum()), "x_sq": float((X * X).sum()),
             "y_head": [float(v) for v in pr.y[:4]], "y_sum": float(pr.y.sum())}
@@ -52,6 +54,10 @@ def cases():
         # batched chain, n = 512, p = 5120, BF16 X: 8 points of the lambda grid
         # (the four corners and four interior points), 40 MM iterations each
         "config3_mid_r40": (lambda: fi.config(3, scale=0.256), "woodbury", "grid8"),
+        # FLSA (X = I): the 256 x 256 denoising image, lambda = (0, 0.1) and (0, 1)
+        "denoise256": (lambda: fi.denoise(lam2=0.1), "identity", None),
+        "denoise256_r30": (lambda: fi.denoise(lam2=0.1), "identity", None),
+        "denoise256_l1_r30": (lambda: fi.denoise(lam2=1.0), "identity", None),
     }
 
 
@@ -69,10 +75,15 @@ def fixed_iterations(name):
 
 
 def solve(pr, solver, lam1, lam2, log=None, fixed=None):
-    X = pr.X64()
     E = pr.graph.edges
-    f = mm.mm_dense if solver == "dense" else mm.mm_woodbury
     t = time.time()
+    if solver == "identity":
+        def f(X, y, E, l1, l2, eps, **kw):
+            return mm.mm_identity(y, E, l1, l2, eps, **kw)
+        X = None
+    else:
+        X = pr.X64()
+        f = mm.mm_dense if solver == "dense" else mm.mm_woodbury
     if fixed is None:
         r = f(X, pr.y, E, lam1, lam2, pr.eps, tol=1e-13, max_iter=12000)
     else:
@@ -103,7 +114,9 @@ def solve(pr, solver, lam1, lam2, log=None, fixed=None):
 def make(name):
     build, solver, lam = cases()[name]
     pr = build()
-    rec = {"name": name, "problem": pr.name, "n": pr.n, "p": pr.p, "dtype": pr.dtype,
+    n_ = pr.p if isinstance(pr, fi.DenoiseProblem) else pr.n
+    dt_ = "identity" if isinstance(pr, fi.DenoiseProblem) else pr.dtype
+    rec = {"name": name, "problem": pr.name, "n": n_, "p": pr.p, "dtype": dt_,
            "graph": pr.graph.kind, "q1": pr.graph.q1, "q2": pr.graph.q2, "eps": pr.eps,
            "solver": solver, "fingerprint": fingerprint(pr)}
     print(name, pr.name, flush=True)

@@ -90,7 +90,7 @@ def _c_layout():
     fields = {
         "flr_graph": ["kind", "q1", "q2", "edges", "m"],
         "flr_opts": ["max_mm", "max_cg", "min_cg", "precond", "tol_cg", "grid", "inject_stall",
-                     "wait_cycles", "max_refine"],
+                     "wait_cycles", "max_refine", "x_smem", "tol_cg_rel"],
         "flr_stats": ["mm_iters", "f", "ms", "refine_steps", "est_err"],
         "flr_server_opts": [],
         "flr_request": [],
@@ -98,7 +98,7 @@ def _c_layout():
     }
     enums = ["FLR_OK", "FLR_EINVAL", "FLR_ENOMEM", "FLR_ECUDA", "FLR_ENOTCONV", "FLR_EBREAKDOWN",
              "FLR_ENONFINITE", "FLR_ETIMEOUT", "FLR_ENOTIMPL", "FLR_ESCRATCH", "FLR_F64", "FLR_F32",
-             "FLR_BF16", "FLR_F16", "FLR_MEM_DEVICE", "FLR_MEM_HOST", "FLR_E_CHAIN", "FLR_E_LATTICE",
+             "FLR_BF16", "FLR_F16", "FLR_IDENTITY", "FLR_MEM_DEVICE", "FLR_MEM_HOST", "FLR_E_CHAIN", "FLR_E_LATTICE",
              "FLR_E_EDGES", "FLR_PC_AUTO", "FLR_PC_JACOBI", "FLR_PC_TRIDIAG", "FLR_PC_PAPER",
              "FLR_PC_TWOLEVEL"]
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "flr.h"', "int main(void) {"]

@@ -23,4 +23,8 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["unit"] == d["unit"]
-    assert "217 iterations" in d["cpu_baseline"]["sample"]
+    # every reported step ran: 1 step of 1 oracle MM iteration, solves/s extrapolated
+    # from the oracle's own 217 MM iterations to the 1e-6 gap, named in the line
+    assert "217 such iterations" in d["cpu_baseline"]["sample"]
+    assert d["config"]["step"] == "1 MM iteration of the oracle"
+    assert abs(d["value"] * d["ms_per_step"] / 1000.0 * 217 - 1.0) < 1e-9

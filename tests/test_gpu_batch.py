@@ -79,3 +79,42 @@ def test_batch_more_than_32_rhs(flr):
         l1, l2 = grid[k]
         ref = mm.mm_dense(X64, pr.y, pr.graph.edges, l1, l2, pr.eps, tol=1e-13)
         assert abs(sts[k].f - ref.f) / abs(ref.f) <= 1e-6, (k, sts[k], ref.f)
+
+
+def test_batch_mid_size_iterates_match_oracle(flr):
+    """The batched chain at n = 512, p = 5120 (BF16 X), 8 points of the 8 x 8 lambda
+    grid including its four corners, 40 MM iterations each, against the Woodbury
+    oracle's iterates (tests/golden/config3_mid_r40.json): beta(40) to 1e-4 of
+    max |beta| element by element and f(beta(40)) to 1e-6 (measured: a few 1e-9
+    where f still changes by 1e-4 per MM iteration).
+
+    At this size the tensor-core pipeline runs its real code paths: phase C
+    reduces over n = 512 in 8 chunks of 64, more than its 3 stages, so every
+    tile recycles stages through the mbarrier waits and parity flips, and
+    phase A splits p over 27 chunks of 192 per 128-row tile.  Each surrogate
+    is solved to an FP64 true residual of 1e-12 (max_refine), so the GPU's
+    iterates follow the exact MM map."""
+    import json, os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "config3_mid_r40.json")) as fh:
+        g = json.load(fh)
+    pr = fi.config(3, scale=0.256)
+    assert (pr.n, pr.p) == (g["n"], g["p"]) == (512, 5120)
+    assert abs(pr.X64().sum() - g["fingerprint"]["x_sum"]) <= 1e-6 * abs(g["fingerprint"]["x_sum"])
+    sols = g["solutions"]
+    l1 = np.array([s_["lam1"] for s_ in sols])
+    l2 = np.array([s_["lam2"] for s_ in sols])
+    R = sols[0]["fixed_iterations"]
+    prob = bf16_problem(flr, pr)
+    betas, objs, sts = prob.solve_batch(l1, l2, eps=pr.eps, tol=1e-300, tol_cg=1e-12,
+                                        max_refine=20, max_mm=R, max_cg=20000, check=False)
+    for k, sol in enumerate(sols):
+        assert sts[k].status == flr.FLR_ENOTCONV and sts[k].mm_iters == R, (k, sts[k])
+        ref = np.array(sol["beta"])
+        b = betas[:, k].cpu().numpy()
+        db = np.abs(b - ref).max() / np.abs(ref).max()
+        assert db <= 1e-4, (k, sol["lam1"], sol["lam2"], db, sts[k])
+        df = abs(sts[k].f - sol["f"]) / abs(sol["f"])
+        assert df <= 1e-6, (k, sts[k].f, sol["f"])
+        print(f"lambda=({sol['lam1']:.3g},{sol['lam2']:.3g}): max|dbeta|/|beta|inf = {db:.2e}, "
+              f"df/f = {df:.2e}")
+        assert sts[k].refine_steps > 0 and sts[k].cg_relres <= 1e-12, (k, sts[k])

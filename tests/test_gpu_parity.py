@@ -96,8 +96,10 @@ def assert_iterate(flr, prob, pr, g, **kw):
     ref = np.array(g["beta"])
     db = np.abs(b - ref).max() / np.abs(ref).max()
     assert db <= BETA, (db, st)
-    assert abs(st.f - g["f"]) <= 1e-10 * abs(g["f"]), (st.f, g["f"])
+    df = abs(st.f - g["f"]) / abs(g["f"])
+    assert df <= GAP, (st.f, g["f"])
     assert st.refine_steps > 0 and st.cg_relres <= 1e-12, st
+    print(f"iterate R={R}: max|dbeta|/|beta|inf = {db:.2e}, df/f = {df:.2e}")
     return db, st
 
 

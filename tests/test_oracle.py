@@ -305,3 +305,52 @@ def test_served_stream_follows_its_recipe():
         assert 400 <= r.p <= 51000
     assert {r.kind for r in reqs} == {"chain", "lattice", "knn"}
     assert {r.dtype for r in reqs} == {"f32", "bf16"}
+
+
+@pytest.mark.parametrize("kind,lam1,lam2", [("chain", 0.3, 0.8), ("lattice", 0.0, 0.4),
+                                            ("lattice", 0.2, 1.5)])
+def test_identity_oracle_matches_dense_oracle(kind, lam1, lam2):
+    """mm_identity (sparse LU of I + lam1 A + lam2 B) takes the iterates of mm_dense
+    with X = I (dense Cholesky of the same matrix)."""
+    rng = np.random.default_rng(41)
+    if kind == "chain":
+        p, E = 40, fi.chain_edges(40)
+    else:
+        p, E = 42, fi.lattice_edges(6, 7)
+    y = rng.standard_normal(p)
+    a = mm.mm_identity(y, E, lam1, lam2, 1e-6, tol=0.0, max_iter=25, stall_stop=False)
+    b = mm.mm_dense(np.eye(p), y, E, lam1, lam2, 1e-6, tol=0.0, max_iter=25, stall_stop=False)
+    np.testing.assert_allclose(a.beta, b.beta, rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(a.f_trace, b.f_trace, rtol=1e-12)
+
+
+def test_identity_oracle_is_exact_flsa_and_soft_threshold():
+    """X = I: the chain limit is the exact FLSA (dynamic programme); with lam2 = 0 it
+    is soft-thresholding (Eq. soft); both within the eps certificate."""
+    rng = np.random.default_rng(42)
+    p = 80
+    y = np.repeat(rng.standard_normal(8) * 2, 10) + 0.3 * rng.standard_normal(p)
+    E = fi.chain_edges(p)
+    eps = 1e-7
+    r = mm.mm_identity(y, E, 0.2, 0.6, eps, tol=1e-15, max_iter=30000)
+    b_star = exact.flsa_chain(y, 0.2, 0.6)
+    f_star = mm.objective(np.eye(p), y, b_star, 0.2, 0.6, E)
+    assert f_star - 1e-12 <= r.f <= f_star + mm.eps_gap(r.beta, 0.2, 0.6, E, eps) + 1e-9 * f_star
+    assert np.abs(r.beta - b_star).max() < 1e-3
+    s = mm.mm_identity(y, E, 0.7, 0.0, 1e-9, tol=1e-15, max_iter=3000)
+    st = exact.soft_threshold(y, 0.7)
+    f_st = mm.objective(np.eye(p), y, st, 0.7, 0.0, E)
+    assert f_st - 1e-12 <= s.f <= f_st + mm.eps_gap(s.beta, 0.7, 0.0, E, 1e-9) + 1e-12 * f_st
+    # coordinates just above the threshold contract slowly (rate ~0.97 here)
+    np.testing.assert_allclose(s.beta, st, atol=1e-5)
+
+
+def test_denoise_generator_follows_its_recipe():
+    """The image is piecewise constant with values {0.2, 0.5, 0.9, 1.0}, the noise is
+    N(0, sd^2) from the stated seed, and the graph is the q1 x q2 lattice."""
+    d = fi.denoise(32, 48, s=3, noise_sd=0.3)
+    assert d.p == 32 * 48 and d.graph.kind == "lattice" and d.graph.m == 32 * 47 + 31 * 48
+    assert set(np.unique(d.image)) <= {0.2, 0.5, 0.9, 1.0}
+    rng = np.random.default_rng(6003)
+    np.testing.assert_allclose(d.y - d.image, 0.3 * rng.standard_normal(d.p), rtol=0, atol=1e-15)
+    assert fi.denoise(256, 256).p == 65536
