@@ -308,6 +308,15 @@ typedef struct flr_request {
     flr_opts opts;          /* opts.grid is capped at grid_per_slot */
     int32_t use_opts;       /* 0: defaults */
     int32_t reserved;
+    uint64_t data_id;       /* 0, or an id the caller gives every request with the same X, y
+                               and E (a lambda path, repeated fits): a slot keeps the handle
+                               of its last such request resident (X already copied to its
+                               column-major layout, X^T y and diag(X^T X) computed) and
+                               reuses it for the next request with the same id, which then
+                               reads none of its own X, y, E.  A resident handle's memory
+                               stays counted against hbm_budget until the slot drops it:
+                               for a request with another id, or when queued work does not
+                               fit otherwise. */
 } flr_request;
 
 typedef struct flr_result {
@@ -318,6 +327,8 @@ typedef struct flr_result {
     int64_t footprint;      /* device bytes reserved for the request */
     uint64_t dev_t0_ns, dev_t1_ns;     /* the GPU's global timer (ns) when the solve kernel
                                           started and finished; comparable between requests */
+    int32_t reused;         /* 1 when the request ran on a slot's resident handle (data_id) */
+    int32_t reserved2;
 } flr_result;
 
 /* Start a server on the current device (opts may be NULL). */

@@ -66,14 +66,16 @@ class FlrRequest(ctypes.Structure):
                 ("n", ctypes.c_int64), ("p", ctypes.c_int64), ("ldx", ctypes.c_int64),
                 ("y", ctypes.c_void_p), ("E", FlrGraph), ("lambda1", ctypes.c_double),
                 ("lambda2", ctypes.c_double), ("eps", ctypes.c_double), ("tol", ctypes.c_double),
-                ("opts", FlrOpts), ("use_opts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("opts", FlrOpts), ("use_opts", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("data_id", ctypes.c_uint64)]
 
 
 class FlrResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32), ("stats", FlrStats),
                 ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
                 ("t_end", ctypes.c_double), ("footprint", ctypes.c_int64),
-                ("dev_t0_ns", ctypes.c_uint64), ("dev_t1_ns", ctypes.c_uint64)]
+                ("dev_t0_ns", ctypes.c_uint64), ("dev_t1_ns", ctypes.c_uint64),
+                ("reused", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class FlrError(RuntimeError):
@@ -337,7 +339,8 @@ class Server:
         self._h = h
         self._keep = {}
 
-    def submit(self, X, y, graph, lam1, lam2, eps=1e-6, tol=1e-9, dtype=None, opts=None, **opt_kw):
+    def submit(self, X, y, graph, lam1, lam2, eps=1e-6, tol=1e-9, dtype=None, opts=None,
+               data_id=0, **opt_kw):
         torch = _torch()
         if X.stride(1) != 1:
             X = X.contiguous()
@@ -353,6 +356,7 @@ class Server:
             keep[-1] = keep[-1].to(X.device)
             r.E.edges = keep[-1].data_ptr()
         r.lambda1, r.lambda2, r.eps, r.tol = float(lam1), float(lam2), float(eps), float(tol)
+        r.data_id = int(data_id)
         if opts is not None or opt_kw:
             r.opts = opts if opts is not None else default_opts(**opt_kw)
             r.use_opts = 1

@@ -258,9 +258,9 @@ flr_status launch_solve_t(flr_handle* h, SolveParams& P, int G, size_t smem) {
   FLR_TRY(max_dynamic_smem((const void*)kern, h->device, &dyn_max));
   if (smem > (size_t)dyn_max) return FLR_ENOTIMPL;
   FLR_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
-  // leading slab columns resident in shared memory (x_smem = 0), the rest streamed
+  // slab columns after the TMEM ones resident in shared memory (x_smem = 0), the rest streamed
   if (P.ws != 0) {
-    P.ws = resident_columns(P.w, P.ldn, sizeof(TX), smem, dyn_max);
+    P.ws = resident_columns(P.w - P.wt, P.ldn, sizeof(TX), smem, dyn_max);
     if (P.ws > 0) smem = (smem + 15) / 16 * 16 + (size_t)P.ws * (size_t)P.ldn * sizeof(TX);
   }
   int nb = 0;
@@ -650,7 +650,11 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   const long long wpad = (w + 3) / 4 * 4;
   const int V = ident ? XT<IdX>::V : (int)(16 / dtype_size(h->dtype));
   const long long q2p = h->gkind == FLR_E_LATTICE ? h->q2 : h->p;
-  const size_t smem = solve_smem_bytes(h->ldn, wpad, V, halo_entries(wpad, q2p, h->p));
+  // X on chip (x_smem = 0): the leading columns of every slab in TMEM, the next
+  // ones in shared memory (sized at launch), the rest streamed
+  const int tct = (o.x_smem == 0 && !ident) ? tmem_cells(h->n, (int)dtype_size(h->dtype)) : 0;
+  const long long trows = tct > 0 ? (h->n + 127) / 128 * 128 : 0;
+  const size_t smem = solve_smem_bytes(h->ldn, wpad, V, halo_entries(wpad, q2p, h->p), trows);
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
@@ -682,6 +686,8 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   P.max_mm = o.max_mm; P.max_cg = o.max_cg; P.min_cg = o.min_cg; P.precond = precond;
   P.max_refine = o.max_refine;
   P.ws = (o.x_smem == 0 && !ident) ? 1 : 0;   // 1: size the resident columns at launch
+  P.tct = tct;
+  P.wt = tct > 0 ? tct * (4 / (int)dtype_size(h->dtype)) : 0;
   P.w = w; P.wpad = wpad; P.levels = levels;
   P.beta_init = binit;
   P.x = h->x; P.z = h->z; P.pb0 = h->pb0; P.pb1 = h->pb1; P.wc = h->wc;

@@ -139,8 +139,8 @@ flr_status run(const SolveParams& P0, const void* Xt, const double* y, long long
   }
   const int dyn_max = optin - (int)fa.sharedSizeBytes;
   if (smem > (size_t)dyn_max) return FLR_ENOTIMPL;
-  if (P.ws != 0) {   // leading slab columns resident in shared memory
-    P.ws = resident_columns(P.w, P.ldn, sizeof(TX), smem, dyn_max);
+  if (P.ws != 0) {   // slab columns after the TMEM ones resident in shared memory
+    P.ws = resident_columns(P.w - P.wt, P.ldn, sizeof(TX), smem, dyn_max);
     if (P.ws > 0) smem = (smem + 15) / 16 * 16 + (size_t)P.ws * (size_t)P.ldn * sizeof(TX);
   }
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess) {
@@ -213,7 +213,9 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   int levels = 0;
   while ((1LL << levels) < w) ++levels;
   const long long wpad = (w + 3) / 4 * 4;
-  const size_t smem = solve_smem_bytes(ldn, wpad, (int)(16 / es), halo_entries(wpad, q2, p));
+  const int tct = o.x_smem == 0 ? tmem_cells(n, (int)es) : 0;
+  const long long trows = tct > 0 ? (n + 127) / 128 * 128 : 0;
+  const size_t smem = solve_smem_bytes(ldn, wpad, (int)(16 / es), halo_entries(wpad, q2, p), trows);
 
   // ---- scratch layout inside the static array
   const size_t vecb = up256(sizeof(double) * (size_t)p);
@@ -259,6 +261,8 @@ extern "C" flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n
   P.max_mm = o.max_mm; P.max_cg = o.max_cg; P.min_cg = o.min_cg; P.precond = precond;
   P.max_refine = o.max_refine;
   P.ws = o.x_smem == 0 ? 1 : 0;
+  P.tct = tct;
+  P.wt = tct > 0 ? tct * (4 / (int)es) : 0;
   P.w = w; P.wpad = wpad; P.levels = levels;
   P.beta_init = nullptr;
   P.x = vec[0]; P.z = vec[1]; P.pb0 = vec[2]; P.pb1 = vec[3];

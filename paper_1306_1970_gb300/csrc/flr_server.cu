@@ -32,11 +32,17 @@ struct Done {
 }  // namespace
 
 struct flr_server {
+  struct Resident {             // a slot's handle kept between requests with one data_id
+    uint64_t id = 0;
+    flr_t h = nullptr;
+    int64_t footprint = 0;
+  };
   flr_server_opts o{};
   int device = 0;
   int sm_count = 0;
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;
+  std::vector<Resident> resident;   // per slot; its footprint stays in in_use
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Job> queue;
@@ -81,33 +87,74 @@ extern "C" int64_t flr_footprint(int64_t n, int64_t p, int64_t m, int32_t dtype,
 
 void flr_server::worker(int slot) {
   cudaSetDevice(device);
+  Resident& res = resident[slot];
   while (true) {
     Job job;
+    bool hit = false;
+    flr_t drop = nullptr;    // a resident handle to release outside the lock
     {
       std::unique_lock<std::mutex> lk(mu);
-      auto pick = [&]() -> bool {
+      // the job this slot would run: one on its resident handle first, else the
+      // oldest whose footprint fits once the slot drops its resident handle
+      auto choose = [&](bool& is_hit) -> std::deque<Job>::iterator {
+        if (res.h)
+          for (auto it = queue.begin(); it != queue.end(); ++it)
+            if (it->r.data_id != 0 && it->r.data_id == res.id) { is_hit = true; return it; }
+        is_hit = false;
+        const int64_t freed = res.h ? res.footprint : 0;
         for (auto it = queue.begin(); it != queue.end(); ++it)
-          if (in_use + it->footprint <= o.hbm_budget) return true;
-        return false;
+          if (in_use - freed + it->footprint <= o.hbm_budget) return it;
+        return queue.end();
       };
-      cv_work.wait(lk, [&] { return pick() || (stopping && queue.empty()); });
-      if (queue.empty()) return;   // stopping
-      auto it = queue.begin();
-      while (in_use + it->footprint > o.hbm_budget) ++it;
-      job = *it;
-      queue.erase(it);
-      in_use += job.footprint;
+      while (true) {
+        if (stopping && queue.empty()) {
+          if (res.h) { in_use -= res.footprint; drop = res.h; res = Resident{}; }
+          lk.unlock();
+          if (drop) flr_destroy(drop);
+          return;
+        }
+        bool h_ = false;
+        auto it = queue.empty() ? queue.end() : choose(h_);
+        if (it != queue.end()) {
+          job = *it;
+          queue.erase(it);
+          hit = h_;
+          if (!hit) {
+            if (res.h) { in_use -= res.footprint; drop = res.h; res = Resident{}; }
+            in_use += job.footprint;
+          }
+          break;
+        }
+        // queued work that fits nowhere while this slot holds a resident handle:
+        // release it so memory frees up
+        if (!queue.empty() && res.h) {
+          in_use -= res.footprint;
+          drop = res.h;
+          res = Resident{};
+          lk.unlock();
+          flr_destroy(drop);
+          drop = nullptr;
+          cv_work.notify_all();
+          lk.lock();
+          continue;
+        }
+        cv_work.wait(lk);
+      }
     }
+    if (drop) flr_destroy(drop);
+    const int64_t held = hit ? res.footprint : job.footprint;   // bytes counted for this handle
     Done d;
     d.res = flr_result{};
     d.res.slot = slot;
     d.res.t_submit = job.t_submit;
     d.res.t_start = now();
     d.res.footprint = job.footprint;
+    d.res.reused = hit ? 1 : 0;
     d.beta.assign((size_t)job.r.p, 0.0);
     const flr_request& r = job.r;
-    flr_t h = nullptr;
-    flr_status st = flr_create(r.X, r.dtype, r.n, r.p, r.ldx, r.y, &r.E, r.mem, streams[slot], &h);
+    flr_t h = hit ? res.h : nullptr;
+    flr_status st = FLR_OK;
+    if (!hit) st = flr_create(r.X, r.dtype, r.n, r.p, r.ldx, r.y, &r.E, r.mem, streams[slot], &h);
     if (st == FLR_OK) {
       flr_opts op;
       flr_default_opts(&op);
@@ -122,13 +169,20 @@ void flr_server::worker(int slot) {
       flr_kernel_span(h, &t0, &t1);
       d.res.dev_t0_ns = t0;
       d.res.dev_t1_ns = t1;
-      flr_destroy(h);
     }
     d.res.status = st;
     d.res.t_end = now();
+    // keep the handle for the next request with this data_id, else release it
+    const bool keep = h && r.data_id != 0 && st != FLR_ECUDA && st != FLR_ETIMEOUT;
+    if (h && !keep) flr_destroy(h);
     {
       std::lock_guard<std::mutex> lk(mu);
-      in_use -= job.footprint;
+      if (keep) {
+        if (!hit) res = Resident{r.data_id, h, held};
+      } else {
+        if (hit) res = Resident{};
+        in_use -= held;
+      }
       done[job.id] = std::move(d);
       pending.erase(job.id);
     }
@@ -166,6 +220,7 @@ extern "C" flr_status flr_server_create(const flr_server_opts* opts, flr_server_
     }
     s->streams.push_back(st);
   }
+  s->resident.assign((size_t)s->o.slots, flr_server::Resident{});
   for (int i = 0; i < s->o.slots; ++i) s->workers.emplace_back(&flr_server::worker, s, i);
   *out = s;
   return FLR_OK;

@@ -63,6 +63,7 @@
 #include <type_traits>
 
 #include "flr_device.cuh"
+#include "flr_tc.cuh"
 
 namespace flr {
 
@@ -105,7 +106,9 @@ struct SolveParams {
   double tol_cg_rel;         // adaptive inner tolerance factor (0 = off)
   int max_mm, max_cg, min_cg, precond;
   int max_refine;            // FP64 residual restarts of the inner solve per MM iteration
-  int ws;                    // leading columns of a block's slab kept in shared memory
+  int ws;                    // slab columns kept in shared memory (after the TMEM ones)
+  int wt;                    // leading slab columns kept in TMEM (0 = none)
+  int tct;                   // TMEM cells per 128-row group (0 = no TMEM)
   long long w, wpad;         // coefficients per block, padded to a multiple of 4
   int levels;                // PCR levels for the block chunk
   const double* beta_init;   // nullptr -> X_j^T y / X_j^T X_j
@@ -166,12 +169,32 @@ inline int resident_columns(long long w, long long ldn, size_t es, size_t base, 
 }
 
 // shared-memory bytes of mm_solve_kernel (the host uses the same formula)
-__host__ __device__ inline size_t solve_smem_bytes(long long ldn, long long wpad, int V, long long nh) {
+__host__ __device__ inline size_t solve_smem_bytes(long long ldn, long long wpad, int V, long long nh,
+                                                   long long trows = 0) {
   return (size_t)ldn * 8 + (size_t)wpad * 8 + (size_t)kThreads * V * 8 + (size_t)wpad * 8 +
          6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 +
          ((size_t)kRF * kThreads + 16) * 8 +
          2 * (size_t)nh * 8 + (size_t)nh * 4 +            // halo p values, 1/q_c, component ids
+         2 * (size_t)trows * 8 + 8 * 32 * 8 +             // TMEM phase A row partials, phase C partials
          (size_t)wpad * 4 + (size_t)wpad;
+}
+
+// ---- X slab columns resident in tensor memory (TMEM).  TMEM is 128 lanes x
+// 512 32-bit columns per SM.  Row i of the slab goes to lane i % 128; row
+// group g = i / 128 takes cells [g * ct, (g + 1) * ct).  A 32-bit cell holds
+// one FP32 element or two 16-bit ones (slab columns 2c and 2c + 1 in its low
+// and high halves).  Warp w of the 8 reads lanes 32 (w % 4) .. + 31 (the
+// hardware's lane quarters) and cells [(w / 4) ct / 2, (w / 4 + 1) ct / 2) of
+// every row group.  Cells per row group (0 = no TMEM): 32 or 64, with at most
+// 32 slab columns per half so phase C keeps 32 accumulators per thread.
+static_assert(kThreads == 256, "the TMEM layout maps 8 warps onto 4 lane quarters x 2 cell halves");
+__host__ __device__ inline int tmem_cells(long long n, int es) {
+  if (es != 4 && es != 2) return 0;
+  const long long R = (n + 127) / 128;
+  long long ct = 512 / R / 32 * 32;
+  const long long cap = 64 / (4 / es);
+  if (ct > cap) ct = cap;
+  return ct >= 32 ? (int)ct : 0;
 }
 
 template <typename TX, typename A>
@@ -215,32 +238,196 @@ __device__ __forceinline__ uint4 lds16(uint32_t a) {
   return r;
 }
 template <typename TX>
-__device__ __forceinline__ uint4 ldx(const TX* __restrict__ Xt, uint32_t xs, int ws, long long ldn,
+__device__ __forceinline__ uint4 ldx(const TX* __restrict__ Xt, uint32_t xs, int wt, int ws, long long ldn,
                                      long long j0, int jj, long long off) {
-  if (jj < ws) return lds16(xs + (uint32_t)(((long long)jj * ldn + off) * (long long)sizeof(TX)));
+  if (jj - wt < ws) return lds16(xs + (uint32_t)(((long long)(jj - wt) * ldn + off) * (long long)sizeof(TX)));
   return ld_stream16(Xt + (j0 + jj) * ldn + off);
+}
+
+// raw 32-bit / 16-bit patterns of X elements
+template <typename TX> __device__ __forceinline__ uint32_t xbits(const TX* p) {
+  if constexpr (sizeof(TX) == 4) return *reinterpret_cast<const uint32_t*>(p);
+  else return (uint32_t)*reinterpret_cast<const unsigned short*>(p);
+}
+// the two elements of a 32-bit cell as A (exact widening)
+template <typename TX, typename A>
+__device__ __forceinline__ void cell2(uint32_t c, A& lo, A& hi) {
+  float a, b;
+  if constexpr (std::is_same<TX, __nv_bfloat16>::value) {
+    a = __uint_as_float(c << 16);
+    b = __uint_as_float(c & 0xffff0000u);
+  } else {
+    const __half2 h2 = *reinterpret_cast<const __half2*>(&c);
+    const float2 f = __half22float2(h2);
+    a = f.x; b = f.y;
+  }
+  lo = (A)a;
+  hi = (A)b;
+}
+
+// Copy the slab's first wt_l columns into TMEM (rows >= n and columns >= wt_l zero).
+template <typename TX>
+__device__ __forceinline__ void tmem_fill(uint32_t tmem, const TX* __restrict__ Xt, long long j0, int wt_l,
+                                          long long n, long long ldn, int ct) {
+  constexpr int cpc = 4 / (int)sizeof(TX);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3, h = warp >> 2, hc = ct / 2;
+  const int R = (int)((n + 127) / 128);
+  for (int g = 0; g < R; ++g) {
+    const long long i = 128LL * g + 32 * q + lane;
+    for (int c0 = 0; c0 < hc; c0 += 16) {
+      uint32_t r[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int cell = h * hc + c0 + e;
+        uint32_t bits = 0;
+#pragma unroll
+        for (int k = 0; k < cpc; ++k) {
+          const int col = cell * cpc + k;
+          if (i < n && col < wt_l) bits |= xbits<TX>(Xt + (j0 + col) * ldn + i) << (16 * k);
+        }
+        r[e] = bits;
+      }
+      tc::tmem_st16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * ct + h * hc + c0), r);
+    }
+  }
+  tc::tmem_wait_st();
+}
+
+// Phase A on the TMEM columns: per-row partial sums of X[:, 0:wt_l] v into
+// tpa[h * trows + i] (h = the warp's cell half), 16 slab columns per load.
+template <typename TX, typename A>
+__device__ __forceinline__ void tmem_phase_a(uint32_t tmem, long long n, int ct, int wt_l, const A* vs,
+                                             A* tpa, long long trows) {
+  constexpr int cpc = 4 / (int)sizeof(TX);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3, h = warp >> 2, hc = ct / 2;
+  const int cph = hc * cpc;   // slab columns per half
+  const int R = (int)((n + 127) / 128);
+  for (int g = 0; g < R; ++g) {
+    A acc = A(0);
+    for (int cb = 0; cb < cph; cb += 16) {
+      const int col0 = h * cph + cb;   // first slab column of this load
+      const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * ct + col0 / cpc);
+      if constexpr (cpc == 1) {
+        uint32_t r[16];
+        tc::tmem_ld16_raw(ta, r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          if (col0 + e < wt_l) acc = fma((A)__uint_as_float(r[e]), vs[col0 + e], acc);
+      } else {
+        uint32_t r[8];
+        tc::tmem_ld8_raw(ta, r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          A lo, hi;
+          cell2<TX, A>(r[e], lo, hi);
+          if (col0 + 2 * e < wt_l) acc = fma(lo, vs[col0 + 2 * e], acc);
+          if (col0 + 2 * e + 1 < wt_l) acc = fma(hi, vs[col0 + 2 * e + 1], acc);
+        }
+      }
+    }
+    tpa[h * trows + 128LL * g + 32 * q + lane] = acc;
+  }
+}
+
+// Phase C on the TMEM columns: tv[jj] = X[:, jj]^T u for jj < wt_l.  In passes
+// of 16 slab columns, each thread accumulates its rows' products, a shuffle
+// reduce-scatter leaves lanes 2c and 2c + 1 halves of the warp's sum for
+// column c of the pass, and the 4 lane quarters add in shared memory (tred,
+// 8 x 32 values).
+template <typename TX, typename A>
+__device__ __forceinline__ void tmem_phase_c(uint32_t tmem, long long n, int ct, int wt_l, const A* us,
+                                             double* tred, double* tv) {
+  constexpr int cpc = 4 / (int)sizeof(TX);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3, h = warp >> 2, hc = ct / 2;
+  const int cph = hc * cpc;   // slab columns per half (<= 32, a multiple of 16)
+  const int R = (int)((n + 127) / 128);
+  for (int cb = 0; cb < cph; cb += 16) {
+    A acc[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[e] = A(0);
+    const uint32_t ta0 = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * hc + cb / cpc);
+    for (int g = 0; g < R; ++g) {
+      const long long i = 128LL * g + 32 * q + lane;
+      const A ui = i < n ? us[i] : A(0);
+      if constexpr (cpc == 1) {
+        uint32_t r[16];
+        tc::tmem_ld16_raw(ta0 + (uint32_t)(g * ct), r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = fma((A)__uint_as_float(r[e]), ui, acc[e]);
+      } else {
+        uint32_t r[8];
+        tc::tmem_ld8_raw(ta0 + (uint32_t)(g * ct), r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          A lo, hi;
+          cell2<TX, A>(r[e], lo, hi);
+          acc[2 * e] = fma(lo, ui, acc[2 * e]);
+          acc[2 * e + 1] = fma(hi, ui, acc[2 * e + 1]);
+        }
+      }
+    }
+    // reduce-scatter of 16 values over the 32 lanes: after the step with offset
+    // o a lane keeps the half whose column index has the lane's bit o; column
+    // bits 3..0 follow lane bits 4..1, and lanes l, l ^ 1 end with halves
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      const int o = 16 >> st, m = 16 >> st;
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int k = 0; k < m / 2; ++k) {
+        const A send = up ? acc[k] : acc[k + m / 2];
+        const A keep = up ? acc[k + m / 2] : acc[k];
+        acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+    if ((lane & 1) == 0) tred[(q * 2 + h) * 32 + cb + (lane >> 1)] = (double)acc[0];
+  }
+  __syncthreads();
+  for (int jj = threadIdx.x; jj < wt_l; jj += kThreads) {
+    const int hh = jj / cph, c = jj - hh * cph;
+    tv[jj] = ((tred[(0 * 2 + hh) * 32 + c] + tred[(1 * 2 + hh) * 32 + c]) +
+              (tred[(2 * 2 + hh) * 32 + c] + tred[(3 * 2 + hh) * 32 + c]));
+  }
+  __syncthreads();
 }
 
 // u[0:n] += sum_{j in slab} X[:, j] * v[j - j0]   (v staged in shared memory)
 template <typename TX, typename A>
 __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restrict__ Xt, uint32_t xs,
-                                        long long j0, int wl, const A* vs, A* red, A* u) {
-  const int ws = P.ws;
+                                        uint32_t tmem, A* tpa, long long j0, int wl, const A* vs, A* red,
+                                        A* u) {
+  const int ws = P.ws, wt = P.wt;
   constexpr int V = XT<TX>::V;
   const int tid = threadIdx.x;
   const int nv = (int)(P.ldn / V);
   if (wl <= 0) return;
+  const int wt_l = wt < wl ? wt : wl;   // this block's TMEM columns
+  const long long trows = (P.n + 127) / 128 * 128;
+  if (wt_l > 0) {
+    if constexpr (sizeof(TX) == 4 || sizeof(TX) == 2) tmem_phase_a<TX, A>(tmem, P.n, P.tct, wt_l, vs, tpa, trows);
+    __syncthreads();
+  }
+  // per-row TMEM partials (zero without TMEM)
+  auto tp = [&](long long i) -> A { return (wt_l > 0 && i < trows) ? tpa[i] + tpa[trows + i] : A(0); };
   if (nv >= kThreads) {
     for (int rv = tid; rv < nv; rv += kThreads) {
       A acc[V];
 #pragma unroll
-      for (int e = 0; e < V; ++e) acc[e] = A(0);
+      for (int e = 0; e < V; ++e) acc[e] = tp((long long)rv * V + e);
       const long long off = (long long)rv * V;
-      int j = 0;
+      int j = wt_l;
       for (; j + kLA <= wl; j += kLA) {
         uint4 raw[kLA];
 #pragma unroll
-        for (int k = 0; k < kLA; ++k) raw[k] = ldx<TX>(Xt, xs, ws, P.ldn, j0, j + k, off);
+        for (int k = 0; k < kLA; ++k) raw[k] = ldx<TX>(Xt, xs, wt, ws, P.ldn, j0, j + k, off);
 #pragma unroll
         for (int k = 0; k < kLA; ++k) {
           A xv[V];
@@ -252,7 +439,7 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
       }
       for (; j < wl; ++j) {
         A xv[V];
-        cvt_to<TX, A>(ldx<TX>(Xt, xs, ws, P.ldn, j0, j, off), xv);
+        cvt_to<TX, A>(ldx<TX>(Xt, xs, wt, ws, P.ldn, j0, j, off), xv);
         const A s = vs[j];
 #pragma unroll
         for (int e = 0; e < V; ++e) acc[e] = fma(xv[e], s, acc[e]);
@@ -271,11 +458,11 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
     for (int e = 0; e < V; ++e) acc[e] = A(0);
     if (cg < ncg) {
       const long long off = (long long)rv * V;
-      int j = cg;
+      int j = wt_l + cg;
       for (; j + (kLA - 1) * ncg < wl; j += kLA * ncg) {
         uint4 raw[kLA];
 #pragma unroll
-        for (int k = 0; k < kLA; ++k) raw[k] = ldx<TX>(Xt, xs, ws, P.ldn, j0, j + k * ncg, off);
+        for (int k = 0; k < kLA; ++k) raw[k] = ldx<TX>(Xt, xs, wt, ws, P.ldn, j0, j + k * ncg, off);
 #pragma unroll
         for (int k = 0; k < kLA; ++k) {
           A xv[V];
@@ -287,7 +474,7 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
       }
       for (; j < wl; j += ncg) {
         A xv[V];
-        cvt_to<TX, A>(ldx<TX>(Xt, xs, ws, P.ldn, j0, j, off), xv);
+        cvt_to<TX, A>(ldx<TX>(Xt, xs, wt, ws, P.ldn, j0, j, off), xv);
         const A s = vs[j];
 #pragma unroll
         for (int e = 0; e < V; ++e) acc[e] = fma(xv[e], s, acc[e]);
@@ -298,7 +485,7 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
     __syncthreads();
     const int rows = nv * V;
     for (int i = tid; i < rows; i += kThreads) {
-      A s = A(0);
+      A s = tp(i);
       for (int g = 0; g < ncg; ++g) s += red[g * rows + i];
       if (i < P.n && s != A(0)) atomicAdd(u + i, s);
     }
@@ -310,14 +497,19 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
 // One warp per pair of columns; each lane keeps CPW x UR 16-byte loads in flight.
 template <typename TX, typename A>
 __device__ __forceinline__ void phase_c(const SolveParams& P, const TX* __restrict__ Xt, uint32_t xs,
-                                        long long j0, int wl, const A* us, double* tv) {
-  const int ws = P.ws;
+                                        uint32_t tmem, double* tred, long long j0, int wl, const A* us,
+                                        double* tv) {
+  const int ws = P.ws, wt = P.wt;
+  const int wt_l = wt < wl ? wt : wl;   // this block's TMEM columns
+  if (wt_l > 0) {
+    if constexpr (sizeof(TX) == 4 || sizeof(TX) == 2) tmem_phase_c<TX, A>(tmem, P.n, P.tct, wt_l, us, tred, tv);
+  }
   constexpr int V = XT<TX>::V;
   constexpr int CPW = 2;  // columns per warp
   constexpr int UR = 4;   // row vectors per lane per round
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nv = (int)(P.ldn / V);
-  for (int base = warp * CPW; base < wl; base += kWarps * CPW) {
+  for (int base = wt_l + warp * CPW; base < wl; base += kWarps * CPW) {
     A acc[CPW];
 #pragma unroll
     for (int c = 0; c < CPW; ++c) acc[c] = A(0);
@@ -329,7 +521,7 @@ __device__ __forceinline__ void phase_c(const SolveParams& P, const TX* __restri
         for (int u = 0; u < UR; ++u) {
           const int rv = rv0 + 32 * u;
           if (base + c < wl && rv < nv)
-            raw[c][u] = ldx<TX>(Xt, xs, ws, P.ldn, j0, base + c, (long long)rv * V);
+            raw[c][u] = ldx<TX>(Xt, xs, wt, ws, P.ldn, j0, base + c, (long long)rv * V);
         }
 #pragma unroll
       for (int u = 0; u < UR; ++u) {
@@ -538,7 +730,7 @@ __device__ __forceinline__ double edge_w(double xj, double xk, double eps) {
 }
 
 template <typename TX, int GK>
-__global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams P) {
+__device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tmem) {
   using Acc = typename XT<TX>::Acc;
   constexpr int V = XT<TX>::V;
   // X = I: n = p, X^T y = y, X^T X = I; the X products become the vector itself
@@ -565,11 +757,14 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
   const long long nh = halo_entries(wp, q2, p);
   double* hv = rs + kRF * kThreads + 16;                    // nh: p at the remote neighbours
   double* hq = hv + nh;                                     // nh: their 1/q_c
-  int* cid_s = reinterpret_cast<int*>(hq + nh);                                   // wpad
+  const long long trows = P.tct > 0 ? (n + 127) / 128 * 128 : 0;
+  double* tpa = hq + nh;                                    // 2*trows: TMEM phase A row partials
+  double* tred = tpa + 2 * trows;                           // 8*32: TMEM phase C partials
+  int* cid_s = reinterpret_cast<int*>(tred + 8 * 32);                             // wpad
   int* hc = cid_s + wp;                                                           // nh
   unsigned char* nb = reinterpret_cast<unsigned char*>(hc + nh);                  // wpad
   // ws leading columns of the slab, resident for the whole solve (16-byte aligned)
-  const size_t xs_off = (solve_smem_bytes(P.ldn, wp, V, nh) + 15) / 16 * 16;
+  const size_t xs_off = (solve_smem_bytes(P.ldn, wp, V, nh, trows) + 15) / 16 * 16;
   const uint32_t xs_sh = (uint32_t)__cvta_generic_to_shared(smraw) + (uint32_t)xs_off;
   // The component sums of r of the last CG iteration, copied to shared memory
   // after its barrier 2 when nc <= kThreads * V; they share the phase A partials'
@@ -633,11 +828,15 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
                    (P.precond == PC_TRIDIAG || P.precond == PC_PAPER || (two && P.q2 >= P.p));
   const int lane = tid & 31, warp = tid >> 5;
 
-  // ---- the shared-memory copy of the slab's first ws columns
+  // ---- the slab's first wt columns into TMEM, the next ws into shared memory
+  if constexpr (sizeof(TX) == 4 || sizeof(TX) == 2) {
+    if (P.tct > 0) tmem_fill<TX>(tmem, Xt, j0, P.wt < wl ? P.wt : wl, n, P.ldn, P.tct);
+  }
   if constexpr (!IDX) {
-    const int wsl = P.ws < wl ? P.ws : wl;   // the last block may own fewer columns
+    const int left = wl - P.wt;               // the last block may own fewer columns
+    const int wsl = P.ws < left ? P.ws : (left > 0 ? left : 0);
     const long long nvec = (long long)wsl * P.ldn * (long long)sizeof(TX) / 16;
-    const uint4* src = reinterpret_cast<const uint4*>(Xt + j0 * P.ldn);
+    const uint4* src = reinterpret_cast<const uint4*>(Xt + (j0 + P.wt) * P.ldn);
     uint4* dst = reinterpret_cast<uint4*>(smraw + xs_off);
     for (long long v = tid; v < nvec; v += kThreads) dst[v] = __ldg(src + v);
   }
@@ -740,7 +939,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
     if constexpr (!IDX) {
       zero_u(U1);
       if (!u0_ready)
-        phase_a<TX, double>(P, Xt, xs_sh, j0, wl, vsd, redd, reinterpret_cast<double*>(U0) + (long long)rep * P.ldn);
+        phase_a<TX, double>(P, Xt, xs_sh, tmem, tpa, j0, wl, vsd, redd, reinterpret_cast<double*>(U0) + (long long)rep * P.ldn);
     } else {
       for (int jj = tid; jj < wl; jj += kThreads) {
         const double d = P.y[j0 + jj] - xs[jj];
@@ -771,7 +970,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
     // inner tolerance of this MM iteration
     const double tol_in = fmax(P.tol_cg, P.tol_cg_rel * (mm > 0 ? rel : 1.0));
     // ---------------- r0 = c - Q x0 (FP64), z0 = M^-1 r0, p1 = z0 (Algorithm 2)
-    if constexpr (!IDX) phase_c<TX, double>(P, Xt, xs_sh, j0, wl, usd, tv);
+    if constexpr (!IDX) phase_c<TX, double>(P, Xt, xs_sh, tmem, tred, j0, wl, usd, tv);
     else for (int jj = tid; jj < wl; jj += kThreads) tv[jj] = xs[jj];
     for (int jj = tid; jj < wl; jj += kThreads) rsm[jj] = (P.c[j0 + jj] - tv[jj]) - qs[jj];
     __syncthreads();
@@ -984,7 +1183,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
         if constexpr (!IDX) {
           zero_u(Unext);
           __syncthreads();
-          phase_a<TX, Acc>(P, Xt, xs_sh, j0, wl, vs, red, Ucur + (long long)rep * P.ldn * 8 / (long long)sizeof(Acc));
+          phase_a<TX, Acc>(P, Xt, xs_sh, tmem, reinterpret_cast<Acc*>(tpa), j0, wl, vs, red, Ucur + (long long)rep * P.ldn * 8 / (long long)sizeof(Acc));
           double sv1[1] = {sv[0]};
           block_reduce<1>(sv1, rs, ncol);
           if (!grid_sum(sv1)) return;
@@ -1006,7 +1205,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
         __syncthreads();
         if (sc[3] != 0.0) { status = (int)sc[3]; break; }
         const double nu = sc[2];
-        if constexpr (!IDX) phase_c<TX, Acc>(P, Xt, xs_sh, j0, wl, us, tv);
+        if constexpr (!IDX) phase_c<TX, Acc>(P, Xt, xs_sh, tmem, tred, j0, wl, us, tv);
         else for (int jj = tid; jj < wl; jj += kThreads) tv[jj] = ps[jj];
         for (int jj = tid; jj < wl; jj += kThreads) {
           const double xn = fma(nu, ps[jj], xs[jj]);
@@ -1099,7 +1298,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       if constexpr (!IDX) {
         zero_u(ucur ? P.ub0 : P.ub1);
         __syncthreads();
-        phase_a<TX, double>(P, Xt, xs_sh, j0, wl, vsd, redd, reinterpret_cast<double*>(Ux) + (long long)rep * P.ldn);
+        phase_a<TX, double>(P, Xt, xs_sh, tmem, tpa, j0, wl, vsd, redd, reinterpret_cast<double*>(Ux) + (long long)rep * P.ldn);
       }
       if (!gb.sync()) return;
       // the last CG iteration's component sums are no longer read: clear them;
@@ -1111,7 +1310,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       if constexpr (!IDX) {
         (void)stage_u<double>(reinterpret_cast<const double*>(Ux), usd, n, P.ldn, P.y, false);
         __syncthreads();
-        phase_c<TX, double>(P, Xt, xs_sh, j0, wl, usd, tv);
+        phase_c<TX, double>(P, Xt, xs_sh, tmem, tred, j0, wl, usd, tv);
       } else {
         for (int jj = tid; jj < wl; jj += kThreads) tv[jj] = xs[jj];
         __syncthreads();
@@ -1191,6 +1390,29 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
       S->t0_ns = t_kernel0;
       S->t1_ns = global_ns();
     }
+  }
+}
+
+// The solve kernel: the body above, with TMEM allocated around it when the
+// plan keeps X columns there (tct > 0).  Every return of the body comes back
+// here, so TMEM is released on every path.  One CTA per SM (launch bounds and
+// registers), so the 512-column allocation never waits for another CTA of
+// this kernel.
+template <typename TX, int GK>
+__global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams P) {
+  __shared__ uint32_t s_tmem;
+  const bool use_tmem = P.tct > 0;
+  if (use_tmem) {
+    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&s_tmem, 512);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+  }
+  mm_solve_body<TX, GK>(P, use_tmem ? s_tmem : 0u);
+  if (use_tmem) {
+    tc::fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(s_tmem, 512);
   }
 }
 

@@ -93,8 +93,8 @@ def _c_layout():
                      "wait_cycles", "max_refine", "x_smem", "tol_cg_rel"],
         "flr_stats": ["mm_iters", "f", "ms", "refine_steps", "est_err"],
         "flr_server_opts": [],
-        "flr_request": [],
-        "flr_result": ["stats", "t_submit", "footprint", "dev_t0_ns", "dev_t1_ns"],
+        "flr_request": ["opts", "use_opts", "data_id"],
+        "flr_result": ["stats", "t_submit", "footprint", "dev_t0_ns", "dev_t1_ns", "reused"],
     }
     enums = ["FLR_OK", "FLR_EINVAL", "FLR_ENOMEM", "FLR_ECUDA", "FLR_ENOTCONV", "FLR_EBREAKDOWN",
              "FLR_ENONFINITE", "FLR_ETIMEOUT", "FLR_ENOTIMPL", "FLR_ESCRATCH", "FLR_F64", "FLR_F32",

@@ -80,3 +80,27 @@ def test_refuses_oversized_and_malformed(flr):
     beta, res = srv.wait(rid)
     assert res.status == 0 and res.footprint <= 1 << 20
     srv.close()
+
+
+def test_resident_handle_serves_a_lambda_path(flr):
+    """Requests that share X, y and E under one data_id run on the slot's resident
+    handle (no new copy of X), and each result equals the same problem solved alone."""
+    pr = fi.config(2, scale=0.04)
+    X, y = host_X(pr)
+    srv = flr.Server(slots=1, grid_per_slot=16)
+    lams = [(0.05, 0.2), (0.1, 0.1), (0.02, 0.4)]
+    kw = dict(tol_cg=1e-12, max_refine=20, max_mm=30000)
+    ids = [srv.submit(X, y, pr.graph, l1, l2, eps=pr.eps, tol=1e-11, data_id=7, **kw) for l1, l2 in lams]
+    other = srv.submit(X, y, pr.graph, 0.05, 0.2, eps=pr.eps, tol=1e-11, **kw)   # no data_id
+    out = [srv.wait(i) for i in ids]
+    bo, ro = srv.wait(other)
+    srv.close()
+    assert [r.reused for _, r in out] == [0, 1, 1]
+    assert ro.reused == 0 and ro.status == 0
+    alone = flr.Problem(X.cuda(), y.cuda(), pr.graph)
+    for (beta, res), (l1, l2) in zip(out, lams):
+        assert res.status == 0
+        b1, s1 = alone.solve(l1, l2, eps=pr.eps, tol=1e-11, grid=res.stats.grid, **kw)
+        assert abs(res.stats.f - s1.f) <= 1e-8 * abs(s1.f)
+        assert np.abs(beta - b1.cpu().numpy()).max() <= 1e-4 * np.abs(beta).max()
+    assert abs(ro.stats.f - out[0][1].stats.f) <= 1e-8 * abs(ro.stats.f)
