@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=24, help="served stream length (serve5)")
+    ap.add_argument("--p-hi", type=int, default=50000, help="largest p of the served stream")
     ap.add_argument("--served-slots", type=int, default=4,
                     help="concurrent copies for the served-form measurement (0 = skip)")
     ap.add_argument("--slots", type=int, default=4)
@@ -56,8 +57,10 @@ def parse():
     ap.add_argument("--max-mm", type=int, default=20000)
     ap.add_argument("--max-cg", type=int, default=10000)
     ap.add_argument("--grid", type=int, default=0, help="solve-kernel blocks (0 = automatic)")
-    ap.add_argument("--hbm-mm", type=int, default=3,
-                    help="MM iterations of the capped HBM-streaming leg (0 = skip)")
+    ap.add_argument("--hbm-mm", type=int, default=2,
+                    help="MM iterations of the HBM-streaming leg (0 = skip)")
+    ap.add_argument("--hbm-cg", type=int, default=100,
+                    help="CG iterations per MM iteration in the HBM-streaming leg")
     return ap.parse_args()
 
 
@@ -188,8 +191,9 @@ def algorithmic_bytes(st, n, p, m, bx):
 
 def hbm_leg(args, dev, peak, peak_kind):
     """The HBM-streaming case: the 250 x 400 lattice, n = 5000, FP16 X (1.0 GB, far
-    larger than L2), a solve capped at `--hbm-mm` MM iterations, timed with CUDA
-    events on the solve's stream.  Algorithmic bytes as for the main workload:
+    larger than L2; the one-pass chunked Q-apply), a solve of exactly --hbm-mm MM
+    iterations of --hbm-cg CG iterations each (inner tolerance out of reach), timed
+    by the kernel's CUDA events.  Algorithmic bytes as for the main workload:
     (CG iterations + MM iterations) Q-applies of n*p*2 + 64p + 16m + 8n bytes."""
     import torch
     import flr_inputs as fi
@@ -198,8 +202,8 @@ def hbm_leg(args, dev, peak, peak_kind):
     X = torch.from_numpy(pr.X).to(dev)
     prob = flr.Problem(X, torch.from_numpy(pr.y).to(dev), pr.graph)
     del X
-    opts = flr.default_opts(tol_cg=args.tol_cg, max_mm=args.hbm_mm, precond=args.precond,
-                            tol_cg_rel=args.tol_cg_rel)
+    opts = flr.default_opts(tol_cg=1e-15, max_mm=args.hbm_mm, max_cg=args.hbm_cg,
+                            min_cg=args.hbm_cg, precond=args.precond)
     stream = torch.cuda.current_stream(dev)
     prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=args.tol, opts=opts, check=False)   # warm-up
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -219,8 +223,8 @@ def hbm_leg(args, dev, peak, peak_kind):
             "mm_iters": st.mm_iters, "cg_iters": st.cg_iters, "kernel_ms": st.ms, "event_ms": ms,
             "us_per_cg_iteration": 1000.0 * st.ms / max(1, st.cg_iters + st.mm_iters),
             "algorithmic_bytes_per_launch": float(alg),
-            "note": f"solve capped at {args.hbm_mm} MM iterations (status {st.status}); "
-                    "X streams from HBM every CG iteration"}
+            "note": f"{args.hbm_mm} MM iterations x {args.hbm_cg} CG iterations (status {st.status}); "
+                    "X streams from HBM once per CG iteration (row chunks re-read from L2)"}
 
 
 def cpu_baseline(pr, golden, budget_s):
@@ -339,28 +343,31 @@ def solve_chain3(args):
 
 
 def serve5(args):
-    """Served mixed stream: closed loop (all requests queued at once) for the capacity,
-    then Poisson arrivals at 0.8 x capacity for p50/p99 latency (submit to done).
-    p log-uniform in [500, 5000], n = p/4, FP32 or BF16 X, chain / lattice / 5-NN."""
+    """Served mixed stream (the recipe of flr_inputs.served_stream: p log-uniform in
+    [500, 5e4], n = p/4, FP32 or BF16, chain / lattice / 5-NN, lambdas log-uniform
+    in [1e-3, 1]); inputs generated on the GPU and resident before the clock starts.
+    Closed loop (all requests queued at once) gives the capacity; then Poisson
+    arrivals at 0.8 x capacity give p50/p99 latency (submit to result)."""
     import threading
     import torch
     import flr_inputs as fi
     import paper_1306_1970_gb300 as flr
     flr.load(build_if_missing=True)
-    reqs = fi.served_stream(args.requests, seed=5000, p_lo=500, p_hi=5000)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    reqs = fi.served_stream(args.requests, seed=5000, p_lo=500, p_hi=args.p_hi)
     data = []
     for r in reqs:
-        pr = fi.request_problem(r)
-        X = torch.from_numpy(np.ascontiguousarray(pr.X))
-        if pr.dtype == "bf16":
+        X, y, g, _ = fi.request_problem_device(r, dev)
+        if r.dtype == "bf16":
             X = X.view(torch.int16)
-        data.append((r, pr, X.pin_memory(), torch.from_numpy(pr.y).pin_memory()))
+        data.append((r, X, y, g))
+    torch.cuda.synchronize()
+    kw = dict(tol_cg=args.tol_cg, max_mm=args.max_mm, tol_cg_rel=args.tol_cg_rel)
 
     def submit(srv, item):
-        r, pr, X, y = item
-        return srv.submit(X, y, pr.graph, r.lam1, r.lam2, eps=pr.eps, tol=args.tol,
-                          dtype="bf16" if pr.dtype == "bf16" else None, tol_cg=args.tol_cg,
-                          max_mm=args.max_mm)
+        r, X, y, g = item
+        return srv.submit(X, y, g, r.lam1, r.lam2, eps=1e-6, tol=args.tol,
+                          dtype="bf16" if r.dtype == "bf16" else None, **kw)
 
     srv = flr.Server(slots=args.slots)
     t0 = time.perf_counter()
@@ -385,19 +392,27 @@ def serve5(args):
     th = threading.Thread(target=feeder)
     th.start()
     th.join()
-    lat, statuses = [], []
-    for i in ids:
+    lat, statuses, per = [], [], []
+    for r, i in zip(reqs, ids):
         _, rr = srv.wait(i)
         lat.append(rr.t_end - rr.t_submit)
         statuses.append(rr.status)
+        per.append({"p": r.p, "n": r.n, "kind": r.kind, "dtype": r.dtype, "status": rr.status,
+                    "mm": rr.stats.mm_iters, "cg": rr.stats.cg_iters, "latency_s": rr.t_end - rr.t_submit,
+                    "kernel_ms": rr.stats.ms})
     opened = time.perf_counter() - start
     srv.close()
-    print(json.dumps({"once": "serve5", "requests": len(data), "slots": args.slots,
-                      "closed_loop_fits_per_s": cap, "open_loop_rate": rate,
-                      "open_loop_fits_per_s": len(data) / opened,
-                      "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                      "status_ok": int(sum(1 for s in statuses if s == 0)),
-                      "closed_status_ok": int(sum(1 for r in res if r.status == 0))}))
+    out = {"requests": len(data), "slots": args.slots, "p_range": [500, args.p_hi],
+           "closed_loop_fits_per_s": cap, "closed_loop_s": closed, "open_loop_rate": rate,
+           "open_loop_fits_per_s": len(data) / opened,
+           "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+           "status_ok": int(sum(1 for s_ in statuses if s_ == 0)),
+           "closed_status_ok": int(sum(1 for r_ in res if r_.status == 0))}
+    if args.once == "serve5":
+        out["once"] = "serve5"
+        out["per_request"] = per
+        print(json.dumps(out))
+    return out
 
 
 def solve_once(args):

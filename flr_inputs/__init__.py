@@ -420,6 +420,50 @@ def served_stream(count: int, seed: int = 5000, p_lo: int = 500, p_hi: int = 500
     return out
 
 
+def request_graph_and_pattern(req: Request):
+    """E and the true coefficients of a served request (host; the k-NN graph by a
+    k-d tree for large p, the recipe's Euclidean neighbours)."""
+    rng = np.random.default_rng(req.seed)
+    p = req.p
+    if req.kind == "chain":
+        return Graph("chain", p), beta_c2(p), rng
+    if req.kind == "lattice":
+        B = np.zeros((req.q1, req.q2))
+        B[req.q1 // 4: req.q1 // 2, req.q2 // 4: 3 * req.q2 // 4] = 1.0
+        return Graph("lattice", p, req.q1, req.q2), B.ravel(), rng
+    pts = rng.uniform(0.0, 1.0, (p, 2))
+    if p <= 4096:
+        e = knn_edges(pts, 5)
+    else:
+        from scipy.spatial import cKDTree
+        _, nb = cKDTree(pts).query(pts, k=6)
+        rows = np.repeat(np.arange(p, dtype=np.int64), 5)
+        cols = nb[:, 1:].reshape(-1).astype(np.int64)
+        lo, hi = np.minimum(rows, cols), np.maximum(rows, cols)
+        key = np.unique(lo * p + hi)
+        e = np.stack([key // p, key % p], axis=1).astype(np.int64)
+    b = np.where(pts[:, 0] < 0.3, 1.0, np.where(pts[:, 0] > 0.7, -1.0, 0.0))
+    return Graph("edges", p, edges=e), b, rng
+
+
+def request_problem_device(req: Request, device):
+    """A served request generated on the GPU (for the large requests of the stream):
+    X iid N(0,1) from torch's seeded counter-based generator on `device`, stored in
+    the request's dtype; y = X beta + N(0,1) in FP64 from the stored X.  Returns
+    (X stored, y, graph, beta_true) as device tensors."""
+    import torch
+    g, b, _ = request_graph_and_pattern(req)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(req.seed))
+    X = torch.randn((req.n, req.p), generator=gen, device=device, dtype=torch.float32)
+    if req.dtype == "bf16":
+        X = X.to(torch.bfloat16)
+    bt = torch.from_numpy(b).to(device)
+    y = X.to(torch.float64) @ bt
+    y += torch.randn(req.n, generator=gen, device=device, dtype=torch.float64)
+    return X, y, g, b
+
+
 def request_problem(req: Request) -> Problem:
     """Materialise one served request: X, y, E and the true pattern."""
     rng = np.random.default_rng(req.seed)

@@ -128,10 +128,15 @@ typedef struct flr_opts {
                             each surrogate to FP64 accuracy from FP32/BF16/FP16 products, so
                             the iterates follow the MM map of Algorithm 1 (mixed-precision
                             iterative refinement).  flr_solve_batch applies it per RHS. */
-    int32_t x_smem;      /* flr_solve / flr_solve_noalloc: 0 (default) keeps as many leading
-                            columns of each thread block's slab of X in shared memory as fit,
-                            copied once per solve, so the X products read them on chip every
-                            CG iteration; -1 streams every column from global memory. */
+    int32_t x_smem;      /* where the X products read X (flr_solve; flr_solve_noalloc takes 0
+                            or -1).  0 (default): when X fits in L2 (<= 96 MB), the leading
+                            columns of each thread block's slab stay on chip for the whole
+                            solve, in tensor memory (TMEM, 32- and 16-bit X, n <= 2048) and
+                            then in shared memory, the rest streamed; when X is larger, each
+                            CG iteration reads X once in row chunks that stay in L2 between
+                            the X p and X^T u halves of the product (one-pass Q-apply).
+                            -1: every column streamed twice per CG iteration.  1: the
+                            one-pass Q-apply at any size (32- and 16-bit X; for tests). */
     double tol_cg_rel;   /* adaptive inner tolerance (default 0 = off).  With theta = tol_cg_rel
                             > 0, the inner solve of MM iteration r stops at
                             max(tol_cg, theta * rel_r), rel_r the relative change of f that

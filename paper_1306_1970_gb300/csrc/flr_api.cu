@@ -107,7 +107,7 @@ struct flr_handle {
   double *qcinv = nullptr, *qc = nullptr, *qci = nullptr, *sc0 = nullptr, *sc1 = nullptr;
   void* ub0 = nullptr;
   void* ub1 = nullptr;
-  unsigned char* ctl = nullptr;     // barrier counter, error flag, DevStats
+  unsigned char* ctl = nullptr;     // barrier counter, error flag, DevStats; split-barrier counters at 256
   unsigned char hctl[256];          // host copy of ctl (read once per solve)
   unsigned long long span_t0 = 0, span_t1 = 0;   // global timer span of the last solve kernel
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -247,9 +247,9 @@ cudaError_t max_dynamic_smem(const void* kern, int dev, int* out) {
   return cudaSuccess;
 }
 
-template <typename TX, int GK>
+template <typename TX, int GK, bool CH = false>
 flr_status launch_solve_t(flr_handle* h, SolveParams& P, int G, size_t smem) {
-  auto kern = mm_solve_kernel<TX, GK>;
+  auto kern = mm_solve_kernel<TX, GK, CH>;
   // The attribute is per kernel, shared by every thread of the process: set it
   // to the most the device allows next to the kernel's static shared memory
   // (the same value from every caller), never to this launch's size, which a
@@ -274,6 +274,17 @@ flr_status launch_solve_t(flr_handle* h, SolveParams& P, int G, size_t smem) {
 
 flr_status launch_solve(flr_handle* h, SolveParams& P, int G, size_t smem) {
   const int gk = h->gkind == FLR_E_EDGES ? GK_CSR : GK_STENCIL;
+  if (P.chunked) {   // one-pass Q-apply for X larger than L2 (32- and 16-bit X)
+    switch (h->dtype) {
+      case FLR_F32: return gk ? launch_solve_t<float, GK_CSR, true>(h, P, G, smem)
+                              : launch_solve_t<float, GK_STENCIL, true>(h, P, G, smem);
+      case FLR_BF16: return gk ? launch_solve_t<__nv_bfloat16, GK_CSR, true>(h, P, G, smem)
+                               : launch_solve_t<__nv_bfloat16, GK_STENCIL, true>(h, P, G, smem);
+      case FLR_F16: return gk ? launch_solve_t<__half, GK_CSR, true>(h, P, G, smem)
+                              : launch_solve_t<__half, GK_STENCIL, true>(h, P, G, smem);
+    }
+    return FLR_EINVAL;
+  }
   switch (h->dtype) {
     case FLR_F64: return gk ? launch_solve_t<double, GK_CSR>(h, P, G, smem)
                             : launch_solve_t<double, GK_STENCIL>(h, P, G, smem);
@@ -549,7 +560,7 @@ flr_status flr_create(const void* X, int32_t dtype, int64_t n, int64_t p, int64_
   if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->ub0), (size_t)h->ldn * 8 * kUR)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, reinterpret_cast<unsigned char**>(&h->ub1), (size_t)h->ldn * 8 * kUR)) != FLR_OK) return fail(s);
   if ((s = dalloc(h, &h->part, (size_t)2 * kNF * kMaxGrid)) != FLR_OK) return fail(s);
-  if ((s = dalloc(h, &h->ctl, 256)) != FLR_OK) return fail(s);
+  if ((s = dalloc(h, &h->ctl, 512)) != FLR_OK) return fail(s);
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) return fail(FLR_ECUDA);
 
   if (ident) {   // X = I: X^T y = y, diag(X^T X) = 1
@@ -624,7 +635,7 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   flr_default_opts(&o);
   if (opts) o = *opts;
   if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0 ||
-      o.max_refine < 0 || (o.x_smem != 0 && o.x_smem != -1) ||
+      o.max_refine < 0 || o.x_smem < -1 || o.x_smem > 1 ||
       !(o.tol_cg_rel >= 0.0))
     return FLR_EINVAL;
   DeviceGuard dg(h->device);
@@ -652,9 +663,14 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   const long long q2p = h->gkind == FLR_E_LATTICE ? h->q2 : h->p;
   // X on chip (x_smem = 0): the leading columns of every slab in TMEM, the next
   // ones in shared memory (sized at launch), the rest streamed
-  const int tct = (o.x_smem == 0 && !ident) ? tmem_cells(h->n, (int)dtype_size(h->dtype)) : 0;
+  // X larger than L2: the chunked one-pass Q-apply instead (32- and 16-bit X)
+  const bool chunked = !ident && h->dtype != FLR_F64 &&
+                       ((o.x_smem == 0 && use_chunked(h->n, h->p, (int)dtype_size(h->dtype), w)) ||
+                        (o.x_smem == 1 && (w + kCCG - 1) / kCCG <= kCPT));
+  const int tct = (o.x_smem == 0 && !ident && !chunked) ? tmem_cells(h->n, (int)dtype_size(h->dtype)) : 0;
   const long long trows = tct > 0 ? (h->n + 127) / 128 * 128 : 0;
-  const size_t smem = solve_smem_bytes(h->ldn, wpad, V, halo_entries(wpad, q2p, h->p), trows);
+  const size_t smem = solve_smem_bytes(h->ldn, wpad, V, halo_entries(wpad, q2p, h->p), trows,
+                                       chunked ? 1 : 0);
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
@@ -664,6 +680,7 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   DevStats* dst = reinterpret_cast<DevStats*>(h->ctl + 128);
   FLR_TRY(cudaMemsetAsync(h->ctl, 0, 128, h->stream));
   FLR_TRY(cudaMemsetAsync(h->ctl + 128, 0xff, 128, h->stream));   // status -1 until written
+  FLR_TRY(cudaMemsetAsync(h->ctl + 256, 0, 256, h->stream));       // split-barrier counters
   const size_t accsz = (size_t)h->ldn * 8 * kUR;
   FLR_TRY(cudaMemsetAsync(h->ub0, 0, accsz, h->stream));
   FLR_TRY(cudaMemsetAsync(h->ub1, 0, accsz, h->stream));
@@ -685,7 +702,9 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   P.tol_cg_rel = o.tol_cg_rel;
   P.max_mm = o.max_mm; P.max_cg = o.max_cg; P.min_cg = o.min_cg; P.precond = precond;
   P.max_refine = o.max_refine;
-  P.ws = (o.x_smem == 0 && !ident) ? 1 : 0;   // 1: size the resident columns at launch
+  P.ws = (o.x_smem == 0 && !ident && !chunked) ? 1 : 0;   // 1: size the resident columns at launch
+  P.chunked = chunked ? 1 : 0;
+  P.cbar = reinterpret_cast<unsigned*>(h->ctl + 256);
   P.tct = tct;
   P.wt = tct > 0 ? tct * (4 / (int)dtype_size(h->dtype)) : 0;
   P.w = w; P.wpad = wpad; P.levels = levels;

@@ -146,6 +146,58 @@ struct GridBarrier {
 };
 
 // ---------------------------------------------------------------------------
+// Split grid barrier: arrive(s) and wait(s) for s = 0, 1, 2, ... in order, with
+// at most one barrier outstanding between a block's arrive(s + 1) and its
+// wait(s).  Barrier s counts on counter s & 1 (two counters 128 bytes apart,
+// zeroed by the host before the launch), so a block that arrives at s + 1
+// before others arrive at s cannot complete barrier s early.  Waits are
+// bounded as in GridBarrier.
+// ---------------------------------------------------------------------------
+struct SplitBarrier {
+  unsigned* cnt;
+  int* err;
+  unsigned epoch[2];
+  long long timeout;
+
+  __device__ __forceinline__ void arrive(int s) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(cnt + 32 * (s & 1)) : "memory");
+    }
+  }
+  __device__ __forceinline__ bool wait(int s) {
+    __shared__ int s_ok2;
+    const int c = s & 1;
+    epoch[c] += 1;
+    if (threadIdx.x == 0) {
+      const unsigned target = epoch[c] * gridDim.x;
+      const unsigned* ctr = cnt + 32 * c;
+      int ok = 1;
+      const long long t0 = clock64();
+      unsigned spins = 0;
+      while (true) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if ((int)(v - target) >= 0) break;
+        if (*((volatile int*)err) != DERR_NONE) { ok = 0; break; }
+        if (++spins > 32) {
+          __nanosleep(32);
+          if (clock64() - t0 > timeout) {
+            atomicCAS(err, DERR_NONE, DERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      s_ok2 = ok;
+    }
+    __syncthreads();
+    return s_ok2 != 0;
+  }
+};
+
+// ---------------------------------------------------------------------------
 // Deterministic warp reduction (fixed shuffle pattern).
 // ---------------------------------------------------------------------------
 template <typename T>

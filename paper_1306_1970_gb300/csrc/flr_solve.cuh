@@ -89,6 +89,18 @@ constexpr double kStrong = 16.0;   // strong-edge threshold of PC_TWOLEVEL
 
 constexpr int kRF = 3;   // fields per block reduction
 constexpr int kLA = 16;  // 16-byte X loads in flight per thread in phase A
+// One-pass (chunked) Q-apply for X larger than L2: row chunks of kCRV 16-byte
+// row vectors, kCCG column groups, at most kCPT slab columns per thread.
+constexpr int kCRV = 16;
+constexpr int kCCG = kThreads / kCRV;
+constexpr int kCPT = 44;
+constexpr int kLC = 8;    // loads in flight per thread in the chunked passes
+
+// The chunked Q-apply is used when X does not fit in L2 (more than 96 MB) and a
+// thread's share of a slab fits its registers.
+__host__ __device__ inline bool use_chunked(long long n, long long p, int es, long long w) {
+  return (double)n * (double)p * es > 96.0e6 && (w + kCCG - 1) / kCCG <= kCPT;
+}
 constexpr int kUR = 1;   // replicas of each u accumulator: block b adds into replica b % kUR,
                          // spreading the atomics of X p over kUR times more L2 lines
 
@@ -109,6 +121,8 @@ struct SolveParams {
   int ws;                    // slab columns kept in shared memory (after the TMEM ones)
   int wt;                    // leading slab columns kept in TMEM (0 = none)
   int tct;                   // TMEM cells per 128-row group (0 = no TMEM)
+  int chunked;               // one-pass chunked Q-apply (use_chunked)
+  unsigned* cbar;            // its two split-barrier counters (128 bytes apart)
   long long w, wpad;         // coefficients per block, padded to a multiple of 4
   int levels;                // PCR levels for the block chunk
   const double* beta_init;   // nullptr -> X_j^T y / X_j^T X_j
@@ -170,12 +184,13 @@ inline int resident_columns(long long w, long long ldn, size_t es, size_t base, 
 
 // shared-memory bytes of mm_solve_kernel (the host uses the same formula)
 __host__ __device__ inline size_t solve_smem_bytes(long long ldn, long long wpad, int V, long long nh,
-                                                   long long trows = 0) {
+                                                   long long trows = 0, int chunked = 0) {
   return (size_t)ldn * 8 + (size_t)wpad * 8 + (size_t)kThreads * V * 8 + (size_t)wpad * 8 +
          6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 +
          ((size_t)kRF * kThreads + 16) * 8 +
          2 * (size_t)nh * 8 + (size_t)nh * 4 +            // halo p values, 1/q_c, component ids
          2 * (size_t)trows * 8 + 8 * 32 * 8 +             // TMEM phase A row partials, phase C partials
+         (chunked ? (size_t)kCPT * kThreads * 8 : 0) +    // chunked Q-apply: X^T u partials
          (size_t)wpad * 4 + (size_t)wpad;
 }
 
@@ -294,50 +309,70 @@ __device__ __forceinline__ void tmem_fill(uint32_t tmem, const TX* __restrict__ 
   tc::tmem_wait_st();
 }
 
+// TMEM loads wait together: tcgen05.wait::ld covers every load a warp has in
+// flight, so phases A and C issue two loads of 16 slab columns per wait.  The
+// loads are unconditional (indices clamped to valid cells; surplus results are
+// ignored) so their results stay in registers.
+
+// 16 slab columns (16 FP32 cells or 8 cells of 16-bit pairs) of this thread's lane
+template <int CPC>
+__device__ __forceinline__ void tmem_ld_cols16(uint32_t ta, uint32_t (&r)[16]) {
+  if constexpr (CPC == 1) {
+    tc::tmem_ld16_raw(ta, r);
+  } else {
+    tc::tmem_ld8_raw(ta, *reinterpret_cast<uint32_t(*)[8]>(r));
+  }
+}
+
+// A's partial over 16 slab columns starting at col0 of one loaded chunk
+template <typename TX, typename A>
+__device__ __forceinline__ A tmem_dot16(const uint32_t (&r)[16], const A* vs, int col0, int wt_l) {
+  constexpr int cpc = 4 / (int)sizeof(TX);
+  A acc = A(0);
+  if constexpr (cpc == 1) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e)
+      if (col0 + e < wt_l) acc = fma((A)__uint_as_float(r[e]), vs[col0 + e], acc);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      A lo, hi;
+      cell2<TX, A>(r[e], lo, hi);
+      if (col0 + 2 * e < wt_l) acc = fma(lo, vs[col0 + 2 * e], acc);
+      if (col0 + 2 * e + 1 < wt_l) acc = fma(hi, vs[col0 + 2 * e + 1], acc);
+    }
+  }
+  return acc;
+}
+
 // Phase A on the TMEM columns: per-row partial sums of X[:, 0:wt_l] v into
-// tpa[h * trows + i] (h = the warp's cell half), 16 slab columns per load.
+// tpa[h * trows + i] (h = the warp's cell half), one wait per row group.
 template <typename TX, typename A>
 __device__ __forceinline__ void tmem_phase_a(uint32_t tmem, long long n, int ct, int wt_l, const A* vs,
                                              A* tpa, long long trows) {
   constexpr int cpc = 4 / (int)sizeof(TX);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3, h = warp >> 2, hc = ct / 2;
-  const int cph = hc * cpc;   // slab columns per half
+  const int cph = hc * cpc;          // slab columns per half: 16 or 32
   const int R = (int)((n + 127) / 128);
+  const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * hc);
+  const uint32_t off1 = cph > 16 ? (uint32_t)(16 / cpc) : 0u;   // second chunk (or the first again)
   for (int g = 0; g < R; ++g) {
-    A acc = A(0);
-    for (int cb = 0; cb < cph; cb += 16) {
-      const int col0 = h * cph + cb;   // first slab column of this load
-      const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(g * ct + col0 / cpc);
-      if constexpr (cpc == 1) {
-        uint32_t r[16];
-        tc::tmem_ld16_raw(ta, r);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int e = 0; e < 16; ++e)
-          if (col0 + e < wt_l) acc = fma((A)__uint_as_float(r[e]), vs[col0 + e], acc);
-      } else {
-        uint32_t r[8];
-        tc::tmem_ld8_raw(ta, r);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          A lo, hi;
-          cell2<TX, A>(r[e], lo, hi);
-          if (col0 + 2 * e < wt_l) acc = fma(lo, vs[col0 + 2 * e], acc);
-          if (col0 + 2 * e + 1 < wt_l) acc = fma(hi, vs[col0 + 2 * e + 1], acc);
-        }
-      }
-    }
+    uint32_t r0[16], r1[16];
+    tmem_ld_cols16<cpc>(tq + (uint32_t)(g * ct), r0);
+    tmem_ld_cols16<cpc>(tq + (uint32_t)(g * ct) + off1, r1);
+    tc::tmem_wait_ld();
+    A acc = tmem_dot16<TX, A>(r0, vs, h * cph, wt_l);
+    if (cph > 16) acc += tmem_dot16<TX, A>(r1, vs, h * cph + 16, wt_l);
     tpa[h * trows + 128LL * g + 32 * q + lane] = acc;
   }
 }
 
 // Phase C on the TMEM columns: tv[jj] = X[:, jj]^T u for jj < wt_l.  In passes
-// of 16 slab columns, each thread accumulates its rows' products, a shuffle
-// reduce-scatter leaves lanes 2c and 2c + 1 halves of the warp's sum for
-// column c of the pass, and the 4 lane quarters add in shared memory (tred,
-// 8 x 32 values).
+// of 16 slab columns (two row groups per wait), each thread accumulates its
+// rows' products, a shuffle reduce-scatter leaves lanes 2c and 2c + 1 halves of
+// the warp's sum for column c of the pass, and the 4 lane quarters add in shared
+// memory (tred, 8 x 32 values).
 template <typename TX, typename A>
 __device__ __forceinline__ void tmem_phase_c(uint32_t tmem, long long n, int ct, int wt_l, const A* us,
                                              double* tred, double* tv) {
@@ -351,19 +386,13 @@ __device__ __forceinline__ void tmem_phase_c(uint32_t tmem, long long n, int ct,
 #pragma unroll
     for (int e = 0; e < 16; ++e) acc[e] = A(0);
     const uint32_t ta0 = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * hc + cb / cpc);
-    for (int g = 0; g < R; ++g) {
+    auto accum = [&](const uint32_t (&r)[16], int g) {
       const long long i = 128LL * g + 32 * q + lane;
       const A ui = i < n ? us[i] : A(0);
       if constexpr (cpc == 1) {
-        uint32_t r[16];
-        tc::tmem_ld16_raw(ta0 + (uint32_t)(g * ct), r);
-        tc::tmem_wait_ld();
 #pragma unroll
         for (int e = 0; e < 16; ++e) acc[e] = fma((A)__uint_as_float(r[e]), ui, acc[e]);
       } else {
-        uint32_t r[8];
-        tc::tmem_ld8_raw(ta0 + (uint32_t)(g * ct), r);
-        tc::tmem_wait_ld();
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           A lo, hi;
@@ -372,6 +401,15 @@ __device__ __forceinline__ void tmem_phase_c(uint32_t tmem, long long n, int ct,
           acc[2 * e + 1] = fma(hi, ui, acc[2 * e + 1]);
         }
       }
+    };
+    for (int g0 = 0; g0 < R; g0 += 2) {
+      const int g1 = g0 + 1 < R ? g0 + 1 : g0;   // a second row group, or the first again
+      uint32_t r0[16], r1[16];
+      tmem_ld_cols16<cpc>(ta0 + (uint32_t)(g0 * ct), r0);
+      tmem_ld_cols16<cpc>(ta0 + (uint32_t)(g1 * ct), r1);
+      tc::tmem_wait_ld();
+      accum(r0, g0);
+      if (g1 != g0) accum(r1, g1);
     }
     // reduce-scatter of 16 values over the 32 lanes: after the step with offset
     // o a lane keeps the half whose column index has the lane's bit o; column
@@ -729,7 +767,7 @@ __device__ __forceinline__ double edge_w(double xj, double xk, double eps) {
   return 1.0 / (fabs(xj - xk) + eps);
 }
 
-template <typename TX, int GK>
+template <typename TX, int GK, bool CH>
 __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tmem) {
   using Acc = typename XT<TX>::Acc;
   constexpr int V = XT<TX>::V;
@@ -760,11 +798,12 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
   const long long trows = P.tct > 0 ? (n + 127) / 128 * 128 : 0;
   double* tpa = hq + nh;                                    // 2*trows: TMEM phase A row partials
   double* tred = tpa + 2 * trows;                           // 8*32: TMEM phase C partials
-  int* cid_s = reinterpret_cast<int*>(tred + 8 * 32);                             // wpad
+  double* cacc = tred + 8 * 32;                             // chunked: kCPT*kThreads partials
+  int* cid_s = reinterpret_cast<int*>(cacc + (CH ? kCPT * kThreads : 0));         // wpad
   int* hc = cid_s + wp;                                                           // nh
   unsigned char* nb = reinterpret_cast<unsigned char*>(hc + nh);                  // wpad
   // ws leading columns of the slab, resident for the whole solve (16-byte aligned)
-  const size_t xs_off = (solve_smem_bytes(P.ldn, wp, V, nh, trows) + 15) / 16 * 16;
+  const size_t xs_off = (solve_smem_bytes(P.ldn, wp, V, nh, trows, CH ? 1 : 0) + 15) / 16 * 16;
   const uint32_t xs_sh = (uint32_t)__cvta_generic_to_shared(smraw) + (uint32_t)xs_off;
   // The component sums of r of the last CG iteration, copied to shared memory
   // after its barrier 2 when nc <= kThreads * V; they share the phase A partials'
@@ -795,6 +834,7 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
   const TX* Xt = reinterpret_cast<const TX*>(P.Xt);
   const unsigned long long t_kernel0 = (b == 0 && tid == 0) ? global_ns() : 0ull;
   GridBarrier gb{P.bar, P.err, 0u, P.timeout};
+  SplitBarrier sb{P.cbar, P.err, {0u, 0u}, P.timeout};
   int slot = 0;
   const long long zchunk = (n + G - 1) / G;
   const long long zs0 = (long long)b * zchunk;
@@ -1180,17 +1220,133 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
           vs[jj] = (Acc)pj;
         }
         double uu[1] = {0.0};
+        bool tv_done = false;   // the chunked Q-apply leaves X^T u in tv
         if constexpr (!IDX) {
+          if constexpr (CH) {
+            // One pass over X: for row chunk s, phase A of chunk s streams from
+            // HBM and adds into u; after the split barrier of chunk s - 1 (whose
+            // wait overlaps the streaming), phase C of chunk s - 1 re-reads that
+            // chunk from L2.  Each thread owns row vector rv of every chunk and the
+            // slab columns cg, cg + kCCG, ...; its X^T u partials stay in registers
+            // until the end.  p^T S p rides on the barrier of chunk 0.
+            constexpr int Rc = kCRV * V;
+            const int rv = tid % kCRV, cg = tid / kCRV;
+            const int ncols = wl > cg ? (wl - cg + kCCG - 1) / kCCG : 0;
+            const int nch = (int)((n + Rc - 1) / Rc);
+            Acc* red_c = red;
+            zero_u(Unext);
+            if (tid == 0) P.part[((long long)slot * kNF) * G + b] = 0.0;
+            {
+              double sv1[1] = {sv[0]};
+              block_reduce<1>(sv1, rs, ncol);
+              if (tid == 0) P.part[((long long)slot * kNF) * G + b] = sv1[0];
+            }
+            // this thread's X^T u partials: slot c * kThreads + tid of the buffer
+            Acc* tacc = reinterpret_cast<Acc*>(cacc);
+            for (int c = 0; c < kCPT; ++c) tacc[c * kThreads + tid] = Acc(0);
+            double uu_loc = 0.0;
+            auto colptr = [&](int c, long long off) { return Xt + (j0 + cg + (long long)c * kCCG) * P.ldn + off; };
+            bool ok = true;
+            for (int st = 0; st <= nch && ok; ++st) {
+              if (st < nch) {   // phase A of chunk st
+                const long long off = (long long)(st * kCRV + rv) * V;
+                const bool rowok = off < P.ldn;
+                Acc acc[V];
+#pragma unroll
+                for (int e = 0; e < V; ++e) acc[e] = Acc(0);
+#pragma unroll 1
+                for (int c0 = 0; c0 < ncols; c0 += kLC) {
+                  uint4 raw[kLC];
+#pragma unroll
+                  for (int k = 0; k < kLC; ++k)
+                    if (c0 + k < ncols && rowok) raw[k] = ld_stream16(colptr(c0 + k, off));
+#pragma unroll
+                  for (int k = 0; k < kLC; ++k) {
+                    if (c0 + k < ncols && rowok) {
+                      Acc xv[V];
+                      cvt_to<TX, Acc>(raw[k], xv);
+                      const Acc sp = vs[cg + (c0 + k) * kCCG];
+#pragma unroll
+                      for (int e = 0; e < V; ++e) acc[e] = fma(xv[e], sp, acc[e]);
+                    }
+                  }
+                }
+#pragma unroll
+                for (int e = 0; e < V; ++e) red_c[cg * Rc + rv * V + e] = acc[e];
+                __syncthreads();
+                for (int i = tid; i < Rc; i += kThreads) {
+                  Acc sum = Acc(0);
+                  for (int g = 0; g < kCCG; ++g) sum += red_c[g * Rc + i];
+                  const long long row = (long long)st * Rc + i;
+                  if (row < n && sum != Acc(0)) atomicAdd(Ucur + row, sum);
+                }
+                sb.arrive(st);
+              }
+              if (st > 0) {     // phase C of chunk st - 1
+                if (!sb.wait(st - 1)) { ok = false; break; }
+                if (st == 1) {  // p^T S p from the partials published before barrier 0
+                  double v1[1] = {tid < G ? ldcg(&P.part[((long long)slot * kNF) * G + tid]) : 0.0};
+                  block_reduce<1>(v1, rs, G);
+                  sv[0] = v1[0];
+                }
+                const long long off = (long long)((st - 1) * kCRV + rv) * V;
+                const bool rowok = off < P.ldn;
+                Acc ul[V];
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                  const long long row = off + e;
+                  ul[e] = (rowok && row < n) ? ldcg(Ucur + row) : Acc(0);
+                  if (cg == 0) uu_loc = fma((double)ul[e], (double)ul[e], uu_loc);
+                }
+#pragma unroll 1
+                for (int c0 = 0; c0 < ncols; c0 += kLC) {
+                  uint4 raw[kLC];
+#pragma unroll
+                  for (int k = 0; k < kLC; ++k)
+                    if (c0 + k < ncols && rowok) raw[k] = ld_stream16(colptr(c0 + k, off));
+#pragma unroll
+                  for (int k = 0; k < kLC; ++k) {
+                    if (c0 + k < ncols && rowok) {
+                      Acc xv[V];
+                      cvt_to<TX, Acc>(raw[k], xv);
+                      Acc d = Acc(0);
+#pragma unroll
+                      for (int e = 0; e < V; ++e) d = fma(xv[e], ul[e], d);
+                      tacc[(c0 + k) * kThreads + tid] += d;
+                    }
+                  }
+                }
+              }
+            }
+            if (!ok) return;
+            slot ^= 1;
+            // X^T u: sum each column's partials over the kCRV row-vector lanes
+            for (int c = 0; c < kCPT; ++c) {
+              Acc t = tacc[c * kThreads + tid];
+#pragma unroll
+              for (int o = 1; o < kCRV; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+              if (rv == 0 && c < ncols) tv[cg + c * kCCG] = (double)t;
+            }
+            uu[0] = uu_loc;
+            block_reduce<1>(uu, rs, kThreads);
+            tv_done = true;
+          } else {
           zero_u(Unext);
           __syncthreads();
           phase_a<TX, Acc>(P, Xt, xs_sh, tmem, reinterpret_cast<Acc*>(tpa), j0, wl, vs, red, Ucur + (long long)rep * P.ldn * 8 / (long long)sizeof(Acc));
           double sv1[1] = {sv[0]};
           block_reduce<1>(sv1, rs, ncol);
-          if (!grid_sum(sv1)) return;
-          sv[0] = sv1[0];
-          // p^T Q p = ||X p||^2 + p^T S p
-          uu[0] = stage_u<Acc>(Ucur, us, n, P.ldn, P.y, false);
-          block_reduce<1>(uu, rs, kThreads);
+          if (tid == 0) P.part[((long long)slot * kNF) * G + b] = sv1[0];
+          if (!gb.sync()) return;
+          // p^T Q p = ||X p||^2 + p^T S p: the partials of p^T S p and the staging
+          // of u (with its sum of squares) load together, then one block reduction
+          double v2[2] = {tid < G ? ldcg(&P.part[((long long)slot * kNF) * G + tid]) : 0.0,
+                          stage_u<Acc>(Ucur, us, n, P.ldn, P.y, false)};
+          block_reduce<2>(v2, rs, kThreads);
+          slot ^= 1;
+          sv[0] = v2[0];
+          uu[0] = v2[1];
+          }
         } else {
           block_reduce<2>(sv, rs, ncol);
           if (!grid_sum(sv)) return;
@@ -1205,8 +1361,11 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
         __syncthreads();
         if (sc[3] != 0.0) { status = (int)sc[3]; break; }
         const double nu = sc[2];
-        if constexpr (!IDX) phase_c<TX, Acc>(P, Xt, xs_sh, tmem, tred, j0, wl, us, tv);
-        else for (int jj = tid; jj < wl; jj += kThreads) tv[jj] = ps[jj];
+        if constexpr (!IDX) {
+          if (!tv_done) phase_c<TX, Acc>(P, Xt, xs_sh, tmem, tred, j0, wl, us, tv);
+        } else {
+          for (int jj = tid; jj < wl; jj += kThreads) tv[jj] = ps[jj];
+        }
         for (int jj = tid; jj < wl; jj += kThreads) {
           const double xn = fma(nu, ps[jj], xs[jj]);
           xs[jj] = xn;
@@ -1231,23 +1390,38 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
           rzn[1] = fma(rj, rj, rzn[1]);
         }
         block_reduce<2>(rzn, rs, ncol);
-        if (!grid_sum(rzn)) return;
-        if (two) {   // r^T z += sum_c (1_c^T r)^2 / q_c, in the same order in every block
-          double cz[1] = {0.0};
-          for (int c0 = tid; c0 < nc; c0 += 4 * kThreads) {   // 8 loads in flight per thread
-            double sv_[4], qv_[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int c = c0 + u * kThreads;
-              sv_[u] = c < nc ? ldcg(Scur + c) : 0.0;
-              qv_[u] = c < nc ? ldcg(P.qci + c) : 0.0;
-              if (c < nc && sc_smem) scs[c] = sv_[u];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) cz[0] = fma(sv_[u] * sv_[u], qv_[u], cz[0]);
+        if (tid == 0) {
+          P.part[((long long)slot * kNF + 0) * G + b] = rzn[0];
+          P.part[((long long)slot * kNF + 1) * G + b] = rzn[1];
+        }
+        if (!gb.sync()) return;
+        {
+          // the partials of r^T z, r^T r and, with the two-level preconditioner, the
+          // component sums for r^T z += sum_c (1_c^T r)^2 / q_c load together; every
+          // block reduces them in the same order
+          double v3[3] = {0.0, 0.0, 0.0};
+          if (tid < G) {
+            v3[0] = ldcg(&P.part[((long long)slot * kNF + 0) * G + tid]);
+            v3[1] = ldcg(&P.part[((long long)slot * kNF + 1) * G + tid]);
           }
-          block_reduce<1>(cz, rs, kThreads);
-          rzn[0] += cz[0];
+          if (two) {
+            for (int c0 = tid; c0 < nc; c0 += 4 * kThreads) {   // 8 loads in flight per thread
+              double sv_[4], qv_[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int c = c0 + u * kThreads;
+                sv_[u] = c < nc ? ldcg(Scur + c) : 0.0;
+                qv_[u] = c < nc ? ldcg(P.qci + c) : 0.0;
+                if (c < nc && sc_smem) scs[c] = sv_[u];
+              }
+#pragma unroll
+              for (int u = 0; u < 4; ++u) v3[2] = fma(sv_[u] * sv_[u], qv_[u], v3[2]);
+            }
+          }
+          block_reduce<3>(v3, rs, kThreads);
+          slot ^= 1;
+          rzn[0] = v3[0] + v3[2];
+          rzn[1] = v3[1];
         }
         if (tid == 0) sc[4] = rzn[0] / rz;
         __syncthreads();
@@ -1394,11 +1568,12 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
 }
 
 // The solve kernel: the body above, with TMEM allocated around it when the
-// plan keeps X columns there (tct > 0).  Every return of the body comes back
+// plan keeps X columns there (tct > 0).  CH selects the chunked one-pass
+// Q-apply (for X larger than L2; P.chunked must be set).  Every return of the body comes back
 // here, so TMEM is released on every path.  One CTA per SM (launch bounds and
 // registers), so the 512-column allocation never waits for another CTA of
 // this kernel.
-template <typename TX, int GK>
+template <typename TX, int GK, bool CH = false>
 __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams P) {
   __shared__ uint32_t s_tmem;
   const bool use_tmem = P.tct > 0;
@@ -1408,7 +1583,7 @@ __global__ void __launch_bounds__(kThreads, 1) mm_solve_kernel(const SolveParams
     __syncthreads();
     tc::fence_after();
   }
-  mm_solve_body<TX, GK>(P, use_tmem ? s_tmem : 0u);
+  mm_solve_body<TX, GK, CH>(P, use_tmem ? s_tmem : 0u);
   if (use_tmem) {
     tc::fence_before();
     __syncthreads();

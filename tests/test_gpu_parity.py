@@ -197,9 +197,21 @@ def test_config4_q50x80_against_oracle(flr):
     assert_iterate(flr, prob, pr, golden("config4_q50x80_r300"))
 
 
+@pytest.mark.parametrize("x_smem", [1, -1])
+def test_q_apply_variants_match_oracle(flr, x_smem):
+    """The one-pass chunked Q-apply (x_smem = 1: X read once per CG iteration in row
+    chunks of 128, the last one ragged at n = 200) and the two-pass streamed one
+    (x_smem = -1) both give the oracle's MM iterates (50 x 80 lattice, FP16)."""
+    g = golden("config4_q50x80_r300")
+    pr = fi.config(4, scale=0.04)
+    prob = problem(flr, pr)
+    assert_iterate(flr, prob, pr, g, x_smem=x_smem)
+
+
 def test_config4_full_size_is_stationary(flr):
-    """Config 4 at full size (250x400 lattice, n=5000, FP16 X, 1 GB): too large for the
-    oracle's MM, so the property that holds at any size is checked instead.  The
+    """Config 4 at full size (250x400 lattice, n=5000, FP16 X, 1 GB; the one-pass chunked
+    Q-apply): too large for the oracle's MM, so the property that holds at any size
+    is checked instead.  The
     MM limit is a stationary point of f_eps (Lemma 2): the oracle's gradient
     X^T(X b - y) + lam1 A b + lam2 B b at the returned b is ~5e-7 ||X^T y|| for an
     MM stopped at tol 1e-9 (measured on the 20x20 instance); a dropped term or a
