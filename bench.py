@@ -213,9 +213,11 @@ def hbm_leg(args, dev, peak, peak_kind):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    prob.close()
+    if st.status not in (0, 4) or st.ms <= 0:
+        raise RuntimeError(f"HBM leg solve failed: status {st.status}")
     alg = algorithmic_bytes(st, pr.n, pr.p, pr.graph.m, 2)
     achieved = alg / (st.ms / 1000.0) / 1e9
-    prob.close()
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
             "kernel": "mm_solve_kernel<__half, stencil>",

@@ -137,14 +137,17 @@ typedef struct flr_opts {
                             the X p and X^T u halves of the product (one-pass Q-apply).
                             -1: every column streamed twice per CG iteration.  1: the
                             one-pass Q-apply at any size (32- and 16-bit X; for tests). */
-    double tol_cg_rel;   /* adaptive inner tolerance (default 0 = off).  With theta = tol_cg_rel
-                            > 0, the inner solve of MM iteration r stops at
-                            max(tol_cg, theta * rel_r), rel_r the relative change of f that
-                            iteration's outer test just measured (theta at r = 0): early
-                            surrogates, whose solutions are far from the limit, are solved
-                            loosely, later ones to tol_cg.  Every CG iteration still lowers
-                            the surrogate g_eps from its warm start, so f_eps still decreases
-                            monotonically (Prop. 1, Lemma 2); the fixed point is unchanged. */
+    double tol_cg_rel;   /* adaptive inner tolerance (default 0 = off; flr_solve and
+                            flr_solve_noalloc).  With theta = tol_cg_rel > 0, the inner solve
+                            of MM iteration r stops when ||r|| / ||X^T y|| <= max(tol_cg,
+                            min(theta * rel_r, ||r0|| / (2 ||X^T y||))), rel_r the relative
+                            change of f that iteration's outer test just measured (1 at r = 0)
+                            and r0 the solve's start residual: early surrogates, whose
+                            solutions are far from the limit, are solved loosely, later ones
+                            to tol_cg, and every solve at least halves its start residual.
+                            Every CG iteration lowers the surrogate g_eps from its warm start,
+                            so f_eps still decreases monotonically (Prop. 1, Lemma 2); the
+                            fixed point is unchanged. */
 } flr_opts;
 
 typedef struct flr_stats {
@@ -220,6 +223,28 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
 flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const double* lambda2,
                            double eps, double tol, const flr_opts* opts, double* betas,
                            int32_t io_mem, double* objectives, flr_stats* stats);
+
+/* Largest p flr_solve_dense accepts (its two p x p FP64 matrices take 16 p^2 bytes). */
+#define FLR_DENSE_MAX_P 32768
+
+/* Algorithm 1 as the paper states it: the same MM iteration as flr_solve, but
+ * each surrogate system (Eq. lin-sys) is solved by a dense Cholesky
+ * factorization, which the paper recommends for a general edge set (Section 4)
+ * where CG may need many iterations.  Everything is FP64: G = X^T X is formed
+ * once per handle (X widened exactly from its storage type) and kept; each MM
+ * iteration forms Q = G + lambda1 A + lambda2 B, factors Q = L L^T by a blocked
+ * right-looking Cholesky in 64 x 64 tiles, solves L L^T beta = X^T y, and
+ * evaluates f(beta) from X beta.  The stop test is the relative change of f
+ * (tol), at most max_mm MM iterations.  beta_init, beta_out, io_mem and stats as
+ * in flr_solve (stats: cg_iters = 0, grid = 0, ms = host wall time).  The first
+ * call allocates 16 p^2 bytes on the handle's device, released by flr_destroy.
+ * Errors: FLR_EINVAL for invalid arguments; FLR_ENOTIMPL for FLR_IDENTITY X or
+ * p > FLR_DENSE_MAX_P; FLR_EBREAKDOWN when a pivot is not positive (Q not SPD,
+ * e.g. lambda1 = 0 with singular X^T X + lambda2 B); FLR_ENOTCONV at max_mm;
+ * FLR_ENOMEM / FLR_ECUDA. */
+flr_status flr_solve_dense(flr_t h, double lambda1, double lambda2, double eps, double tol,
+                           int32_t max_mm, const double* beta_init, double* beta_out,
+                           int32_t io_mem, flr_stats* stats);
 
 /* Release a handle and everything it owns (NULL is ignored). */
 void flr_destroy(flr_t h);

@@ -31,7 +31,7 @@ DTYPE_CODES = {"f64": FLR_F64, "f32": FLR_F32, "bf16": FLR_BF16, "f16": FLR_F16,
 EXPORTS = ("flr_default_opts", "flr_strerror", "flr_create", "flr_solve", "flr_solve_batch",
            "flr_destroy", "flr_get_info", "flr_solve_noalloc", "flr_server_create",
            "flr_server_submit", "flr_server_poll", "flr_server_wait", "flr_server_destroy",
-           "flr_footprint")
+           "flr_footprint", "flr_solve_dense")
 
 
 class FlrGraph(ctypes.Structure):
@@ -139,6 +139,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.flr_server_destroy.restype = c.c_int32
     lib.flr_footprint.argtypes = [c.c_int64, c.c_int64, c.c_int64, c.c_int32, c.c_int32]
     lib.flr_footprint.restype = c.c_int64
+    lib.flr_solve_dense.argtypes = [c.c_void_p, c.c_double, c.c_double, c.c_double, c.c_double,
+                                    c.c_int32, c.c_void_p, c.c_void_p, c.c_int32, c.POINTER(FlrStats)]
+    lib.flr_solve_dense.restype = c.c_int32
     _LIB = lib
     return lib
 
@@ -289,6 +292,26 @@ class Problem:
         stats.status = st
         if check and st not in (FLR_OK, FLR_ENOTCONV):
             raise FlrError(st, "flr_solve")
+        return out, stats
+
+    def solve_dense(self, lam1: float, lam2: float, eps: float = 1e-6, tol: float = 1e-9,
+                    max_mm: int = 10000, beta_init=None, out=None, check: bool = True):
+        """Algorithm 1 with a dense FP64 Cholesky per MM iteration (flr_solve_dense)."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.p, dtype=torch.float64, device=self.device)
+        mem = FLR_MEM_DEVICE if out.is_cuda else FLR_MEM_HOST
+        bi = None
+        if beta_init is not None:
+            bi = beta_init.to(dtype=torch.float64, device=out.device).contiguous()
+        s = FlrStats()
+        st = self._lib.flr_solve_dense(self._h, float(lam1), float(lam2), float(eps), float(tol),
+                                       int(max_mm), bi.data_ptr() if bi is not None else None,
+                                       out.data_ptr(), mem, ctypes.byref(s))
+        stats = Stats.from_c(s)
+        stats.status = st
+        if check and st not in (FLR_OK, FLR_ENOTCONV):
+            raise FlrError(st, "flr_solve_dense")
         return out, stats
 
     def solve_batch(self, lam1s, lam2s, eps: float = 1e-6, tol: float = 1e-9,

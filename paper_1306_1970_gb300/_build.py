@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libflr.so")
-SOURCES = ["flr_api.cu", "flr_noalloc.cu", "flr_server.cu"]
+SOURCES = ["flr_api.cu", "flr_noalloc.cu", "flr_server.cu", "flr_dense.cu"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC", "-shared"]
 

@@ -110,6 +110,8 @@ struct flr_handle {
   unsigned char* ctl = nullptr;     // barrier counter, error flag, DevStats; split-barrier counters at 256
   unsigned char hctl[256];          // host copy of ctl (read once per solve)
   unsigned long long span_t0 = 0, span_t1 = 0;   // global timer span of the last solve kernel
+  void* aux = nullptr;                            // workspace of another translation unit
+  void (*aux_release)(void*) = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<void*> allocs;
   // batched tensor-core path (allocated on first use)
@@ -178,6 +180,8 @@ void release(flr_handle* h) {
   {
     DeviceGuard dg(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->aux && h->aux_release) h->aux_release(h->aux);
+    h->aux = nullptr;
     for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
     h->allocs.clear();
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -665,12 +669,11 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   // ones in shared memory (sized at launch), the rest streamed
   // X larger than L2: the chunked one-pass Q-apply instead (32- and 16-bit X)
   const bool chunked = !ident && h->dtype != FLR_F64 &&
-                       ((o.x_smem == 0 && use_chunked(h->n, h->p, (int)dtype_size(h->dtype), w)) ||
-                        (o.x_smem == 1 && (w + kCCG - 1) / kCCG <= kCPT));
+                       ((o.x_smem == 0 && use_chunked(h->n, h->p, (int)dtype_size(h->dtype))) ||
+                        o.x_smem == 1);
   const int tct = (o.x_smem == 0 && !ident && !chunked) ? tmem_cells(h->n, (int)dtype_size(h->dtype)) : 0;
   const long long trows = tct > 0 ? (h->n + 127) / 128 * 128 : 0;
-  const size_t smem = solve_smem_bytes(h->ldn, wpad, V, halo_entries(wpad, q2p, h->p), trows,
-                                       chunked ? 1 : 0);
+  const size_t smem = solve_smem_bytes(h->ldn, wpad, V, halo_entries(wpad, q2p, h->p), trows);
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (smem > (size_t)smem_max) return FLR_ENOTIMPL;
@@ -805,6 +808,30 @@ void flr_destroy(flr_t h) { release(h); }
 void flr_kernel_span(flr_t h, unsigned long long* t0, unsigned long long* t1) {
   *t0 = h ? h->span_t0 : 0;
   *t1 = h ? h->span_t1 : 0;
+}
+
+bool flr_get_view(flr_t h, flr_view* v) {
+  if (!h || !v) return false;
+  v->device = h->device;
+  v->sm_count = h->sm_count;
+  v->stream = h->stream;
+  v->dtype = h->dtype;
+  v->n = h->n; v->p = h->p; v->ldn = h->ldn; v->m = h->m;
+  v->gkind = h->gkind;
+  v->q2 = h->gkind == FLR_E_LATTICE ? h->q2 : h->p;
+  v->Xt = h->Xt;
+  v->y = h->y; v->c = h->c; v->d = h->d;
+  v->cnorm = h->cnorm;
+  v->rowptr = h->rowptr;
+  v->col = h->col;
+  return true;
+}
+
+void* flr_aux_get(flr_t h) { return h ? h->aux : nullptr; }
+void flr_aux_set(flr_t h, void* ws, void (*release)(void*)) {
+  if (!h) return;
+  h->aux = ws;
+  h->aux_release = release;
 }
 
 extern "C" {

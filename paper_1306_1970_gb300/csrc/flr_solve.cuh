@@ -90,16 +90,15 @@ constexpr double kStrong = 16.0;   // strong-edge threshold of PC_TWOLEVEL
 constexpr int kRF = 3;   // fields per block reduction
 constexpr int kLA = 16;  // 16-byte X loads in flight per thread in phase A
 // One-pass (chunked) Q-apply for X larger than L2: row chunks of kCRV 16-byte
-// row vectors, kCCG column groups, at most kCPT slab columns per thread.
+// row vectors, kCCG column groups.
 constexpr int kCRV = 16;
 constexpr int kCCG = kThreads / kCRV;
-constexpr int kCPT = 44;
-constexpr int kLC = 8;    // loads in flight per thread in the chunked passes
+constexpr int kLC = 8;    // loads in flight per thread in the chunked phase A
+constexpr int kLCC = 8;   // and in the chunked phase C (a power of two <= kCRV)
 
-// The chunked Q-apply is used when X does not fit in L2 (more than 96 MB) and a
-// thread's share of a slab fits its registers.
-__host__ __device__ inline bool use_chunked(long long n, long long p, int es, long long w) {
-  return (double)n * (double)p * es > 96.0e6 && (w + kCCG - 1) / kCCG <= kCPT;
+// The chunked Q-apply is used when X does not fit in L2 (more than 96 MB).
+__host__ __device__ inline bool use_chunked(long long n, long long p, int es) {
+  return (double)n * (double)p * es > 96.0e6;
 }
 constexpr int kUR = 1;   // replicas of each u accumulator: block b adds into replica b % kUR,
                          // spreading the atomics of X p over kUR times more L2 lines
@@ -184,13 +183,12 @@ inline int resident_columns(long long w, long long ldn, size_t es, size_t base, 
 
 // shared-memory bytes of mm_solve_kernel (the host uses the same formula)
 __host__ __device__ inline size_t solve_smem_bytes(long long ldn, long long wpad, int V, long long nh,
-                                                   long long trows = 0, int chunked = 0) {
+                                                   long long trows = 0) {
   return (size_t)ldn * 8 + (size_t)wpad * 8 + (size_t)kThreads * V * 8 + (size_t)wpad * 8 +
          6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 + 6 * (size_t)wpad * 8 +
          ((size_t)kRF * kThreads + 16) * 8 +
          2 * (size_t)nh * 8 + (size_t)nh * 4 +            // halo p values, 1/q_c, component ids
          2 * (size_t)trows * 8 + 8 * 32 * 8 +             // TMEM phase A row partials, phase C partials
-         (chunked ? (size_t)kCPT * kThreads * 8 : 0) +    // chunked Q-apply: X^T u partials
          (size_t)wpad * 4 + (size_t)wpad;
 }
 
@@ -798,12 +796,11 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
   const long long trows = P.tct > 0 ? (n + 127) / 128 * 128 : 0;
   double* tpa = hq + nh;                                    // 2*trows: TMEM phase A row partials
   double* tred = tpa + 2 * trows;                           // 8*32: TMEM phase C partials
-  double* cacc = tred + 8 * 32;                             // chunked: kCPT*kThreads partials
-  int* cid_s = reinterpret_cast<int*>(cacc + (CH ? kCPT * kThreads : 0));         // wpad
+  int* cid_s = reinterpret_cast<int*>(tred + 8 * 32);                             // wpad
   int* hc = cid_s + wp;                                                           // nh
   unsigned char* nb = reinterpret_cast<unsigned char*>(hc + nh);                  // wpad
   // ws leading columns of the slab, resident for the whole solve (16-byte aligned)
-  const size_t xs_off = (solve_smem_bytes(P.ldn, wp, V, nh, trows, CH ? 1 : 0) + 15) / 16 * 16;
+  const size_t xs_off = (solve_smem_bytes(P.ldn, wp, V, nh, trows) + 15) / 16 * 16;
   const uint32_t xs_sh = (uint32_t)__cvta_generic_to_shared(smraw) + (uint32_t)xs_off;
   // The component sums of r of the last CG iteration, copied to shared memory
   // after its barrier 2 when nc <= kThreads * V; they share the phase A partials'
@@ -1129,6 +1126,11 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
       block_reduce<2>(rz2, rs, ncol);
       if (!grid_sum(rz2)) return;
       double rz = rz2[0], rr = rz2[1], gamma = 0.0;
+      // the adaptive tolerance never lets an inner solve stop before it has halved
+      // its start residual (an inexact-Newton safeguard), so every MM iteration
+      // makes progress
+      // (kept in the shared scalar slot sc[5], read by the deciding thread)
+      if (tid == 0) sc[5] = P.tol_cg_rel > 0.0 ? fmax(P.tol_cg, fmin(tol_in, 0.5 * sqrt(rr) / P.cnorm)) : P.tol_cg;
       ucur ^= 1;
       // ---------------- CG iterations (inner products and scalars in FP64)
       int k = 0;
@@ -1136,7 +1138,7 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
         if (tid == 0) {
           const double rel_r = sqrt(rr) / P.cnorm;
           sc[0] = rel_r;
-          sc[1] = (k >= P.max_cg || (k >= P.min_cg && rel_r <= tol_in)) ? 1.0 : 0.0;
+          sc[1] = (k >= P.max_cg || (k >= P.min_cg && rel_r <= sc[5])) ? 1.0 : 0.0;
         }
         __syncthreads();
         relres = sc[0];
@@ -1227,8 +1229,8 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
             // HBM and adds into u; after the split barrier of chunk s - 1 (whose
             // wait overlaps the streaming), phase C of chunk s - 1 re-reads that
             // chunk from L2.  Each thread owns row vector rv of every chunk and the
-            // slab columns cg, cg + kCCG, ...; its X^T u partials stay in registers
-            // until the end.  p^T S p rides on the barrier of chunk 0.
+            // slab columns cg, cg + kCCG, ....  p^T S p rides on the barrier of
+            // chunk 0.
             constexpr int Rc = kCRV * V;
             const int rv = tid % kCRV, cg = tid / kCRV;
             const int ncols = wl > cg ? (wl - cg + kCCG - 1) / kCCG : 0;
@@ -1241,9 +1243,13 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
               block_reduce<1>(sv1, rs, ncol);
               if (tid == 0) P.part[((long long)slot * kNF) * G + b] = sv1[0];
             }
-            // this thread's X^T u partials: slot c * kThreads + tid of the buffer
-            Acc* tacc = reinterpret_cast<Acc*>(cacc);
-            for (int c = 0; c < kCPT; ++c) tacc[c * kThreads + tid] = Acc(0);
+            // X^T u accumulates in tv: after each chunk, a column's partials are
+            // summed over the kCRV row-vector lanes by shuffles (the two column
+            // groups of a warp loop to the larger count; lanes past their own
+            // count add zeros) and lane rv == 0 adds the sum to tv.
+            const int ncols_w = wl > (cg & ~1) ? (wl - (cg & ~1) + kCCG - 1) / kCCG : 0;
+            if (rv == 0)
+              for (int c = 0; c < ncols; ++c) tv[cg + c * kCCG] = 0.0;
             double uu_loc = 0.0;
             auto colptr = [&](int c, long long off) { return Xt + (j0 + cg + (long long)c * kCCG) * P.ldn + off; };
             bool ok = true;
@@ -1299,34 +1305,52 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
                   if (cg == 0) uu_loc = fma((double)ul[e], (double)ul[e], uu_loc);
                 }
 #pragma unroll 1
-                for (int c0 = 0; c0 < ncols; c0 += kLC) {
-                  uint4 raw[kLC];
+                for (int c0 = 0; c0 < ncols_w; c0 += kLCC) {
+                  uint4 raw[kLCC];
 #pragma unroll
-                  for (int k = 0; k < kLC; ++k)
+                  for (int k = 0; k < kLCC; ++k)
                     if (c0 + k < ncols && rowok) raw[k] = ld_stream16(colptr(c0 + k, off));
+                  Acc d[kLCC];
 #pragma unroll
-                  for (int k = 0; k < kLC; ++k) {
+                  for (int k = 0; k < kLCC; ++k) {
+                    d[k] = Acc(0);
                     if (c0 + k < ncols && rowok) {
                       Acc xv[V];
                       cvt_to<TX, Acc>(raw[k], xv);
-                      Acc d = Acc(0);
 #pragma unroll
-                      for (int e = 0; e < V; ++e) d = fma(xv[e], ul[e], d);
-                      tacc[(c0 + k) * kThreads + tid] += d;
+                      for (int e = 0; e < V; ++e) d[k] = fma(xv[e], ul[e], d[k]);
                     }
                   }
+                  // reduce-scatter over the kCRV lanes: each halving step keeps the
+                  // upper or lower half of the columns, then the remaining lanes of
+                  // a group all-reduce; lane rv ends with column col
+                  int col = 0;
+                  int m = kLCC;
+#pragma unroll
+                  for (int o = kCRV / 2; o >= 1; o >>= 1) {
+                    if (m > 1) {
+                      const bool hi = (rv & o) != 0;
+#pragma unroll
+                      for (int i = 0; i < kLCC / 2; ++i) {
+                        if (i < m / 2) {
+                          const Acc send = hi ? d[i] : d[i + m / 2];
+                          const Acc keep = hi ? d[i + m / 2] : d[i];
+                          d[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                        }
+                      }
+                      if (hi) col += m / 2;
+                      m /= 2;
+                    } else {
+                      d[0] += __shfl_xor_sync(0xffffffffu, d[0], o);
+                    }
+                  }
+                  if ((rv & (kCRV / kLCC - 1)) == 0 && c0 + col < ncols)
+                    tv[cg + (c0 + col) * kCCG] += (double)d[0];
                 }
               }
             }
             if (!ok) return;
             slot ^= 1;
-            // X^T u: sum each column's partials over the kCRV row-vector lanes
-            for (int c = 0; c < kCPT; ++c) {
-              Acc t = tacc[c * kThreads + tid];
-#pragma unroll
-              for (int o = 1; o < kCRV; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-              if (rv == 0 && c < ncols) tv[cg + c * kCCG] = (double)t;
-            }
             uu[0] = uu_loc;
             block_reduce<1>(uu, rs, kThreads);
             tv_done = true;
@@ -1506,7 +1530,7 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
       ++nref_mm;
       ++nref_total;
       relres = sqrt(rr1[0]) / P.cnorm;
-      if (relres <= tol_in) {   // accurate: X x stays in accumulator `ucur` for the next MM iteration
+      if (relres <= sc[5]) {   // accurate: X x stays in accumulator `ucur` for the next MM iteration
         u0_ready = true;
         break;
       }
