@@ -52,7 +52,12 @@ def parse():
     ap.add_argument("--served-slots", type=int, default=4,
                     help="concurrent copies for the served-form measurement (0 = skip)")
     ap.add_argument("--slots", type=int, default=4)
-    ap.add_argument("--once", default=None, choices=["config2", "config4", "batch3", "chain3", "serve5"],
+    ap.add_argument("--stream-requests", type=int, default=16,
+                    help="served-stream requests in the bench line (0 = skip)")
+    ap.add_argument("--stream-rate", type=float, default=1.0, help="offered requests/s")
+    ap.add_argument("--stream-max-mm", type=int, default=3000,
+                    help="MM-iteration cap of each served fit in the bench line")
+    ap.add_argument("--once", default=None, choices=["config2", "config4", "hbm4", "batch3", "chain3", "serve5", "stream"],
                     help="one solve of a workload (for profiler captures), then exit")
     ap.add_argument("--max-mm", type=int, default=20000)
     ap.add_argument("--max-cg", type=int, default=10000)
@@ -114,14 +119,15 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+def ncu_traffic(key):
+    """DRAM bytes per launch of workload `key` from the committed ncu summary, if it was
+    taken from this kernel source."""
     path = os.path.join(ROOT, "profiles", "mm_solve_kernel_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
-        d = json.load(fh)
-    if d.get("source_hash") != kernel_source_hash():
+        d = json.load(fh).get(key)
+    if not d or d.get("source_hash") != kernel_source_hash():
         return None
     return d
 
@@ -189,21 +195,31 @@ def algorithmic_bytes(st, n, p, m, bx):
     return (st.cg_iters + st.mm_iters) * per_apply
 
 
-def hbm_leg(args, dev, peak, peak_kind):
+def hbm_problem(args, dev):
     """The HBM-streaming case: the 250 x 400 lattice, n = 5000, FP16 X (1.0 GB, far
-    larger than L2; the one-pass chunked Q-apply), a solve of exactly --hbm-mm MM
-    iterations of --hbm-cg CG iterations each (inner tolerance out of reach), timed
-    by the kernel's CUDA events.  Algorithmic bytes as for the main workload:
-    (CG iterations + MM iterations) Q-applies of n*p*2 + 64p + 16m + 8n bytes."""
+    larger than L2; the one-pass chunked Q-apply), solved for exactly --hbm-mm MM
+    iterations of --hbm-cg CG iterations each (inner tolerance out of reach)."""
     import torch
     import flr_inputs as fi
     import paper_1306_1970_gb300 as flr
+    flr.load(build_if_missing=True)
     pr = fi.config(4)
     X = torch.from_numpy(pr.X).to(dev)
     prob = flr.Problem(X, torch.from_numpy(pr.y).to(dev), pr.graph)
     del X
     opts = flr.default_opts(tol_cg=1e-15, max_mm=args.hbm_mm, max_cg=args.hbm_cg,
                             min_cg=args.hbm_cg, precond=args.precond)
+    return pr, prob, opts
+
+
+def hbm_leg(args, dev, peak, peak_kind):
+    """The HBM-streaming case (hbm_problem), timed by the kernel's CUDA events after one
+    warm-up solve.  Algorithmic bytes as for the main workload: (CG iterations + MM
+    iterations) Q-applies of n*p*2 + 64p + 16m + 8n bytes.  `traffic` is the DRAM bytes
+    of the same launch (`bench.py --once hbm4` under ncu) when the committed summary
+    matches the kernel source."""
+    import torch
+    pr, prob, opts = hbm_problem(args, dev)
     stream = torch.cuda.current_stream(dev)
     prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=args.tol, opts=opts, check=False)   # warm-up
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -218,15 +234,18 @@ def hbm_leg(args, dev, peak, peak_kind):
         raise RuntimeError(f"HBM leg solve failed: status {st.status}")
     alg = algorithmic_bytes(st, pr.n, pr.p, pr.graph.m, 2)
     achieved = alg / (st.ms / 1000.0) / 1e9
+    tr = ncu_traffic("hbm4")
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-            "kernel": "mm_solve_kernel<__half, stencil>",
+            "frac": achieved / peak, "peak_kind": peak_kind,
+            "traffic": tr["dram_bytes_per_launch"] if tr else None,
+            "kernel": "mm_solve_kernel<__half, stencil, chunked>",
             "workload": "lattice-fp16-250x400-n5000 (1.0 GB X)",
             "mm_iters": st.mm_iters, "cg_iters": st.cg_iters, "kernel_ms": st.ms, "event_ms": ms,
             "us_per_cg_iteration": 1000.0 * st.ms / max(1, st.cg_iters + st.mm_iters),
             "algorithmic_bytes_per_launch": float(alg),
             "note": f"{args.hbm_mm} MM iterations x {args.hbm_cg} CG iterations (status {st.status}); "
-                    "X streams from HBM once per CG iteration (row chunks re-read from L2)"}
+                    "X streams from HBM once per CG iteration (row chunks re-read from L2); "
+                    "each MM iteration's FP64 refinement pass reads X twice more"}
 
 
 def cpu_baseline(pr, golden, budget_s):
@@ -305,7 +324,7 @@ def solve_batch3(args):
     t0 = time.perf_counter()
     betas, objs, sts = prob.solve_batch(grid[:, 0], grid[:, 1], eps=pr.eps, tol=args.tol,
                                         tol_cg=args.tol_cg, max_mm=args.max_mm, max_cg=args.max_cg,
-                                        check=False)
+                                        tol_cg_rel=args.tol_cg_rel, check=False)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
     out = {"once": "batch3", "K": len(grid), "seconds": tb, "kernel_ms": sts[0].ms,
@@ -315,7 +334,8 @@ def solve_batch3(args):
     for k in (0, 27, 63):
         t0 = time.perf_counter()
         _, s1 = prob.solve(grid[k, 0], grid[k, 1], eps=pr.eps, tol=args.tol, tol_cg=args.tol_cg,
-                           max_mm=args.max_mm, max_cg=args.max_cg, check=False)
+                           max_mm=args.max_mm, max_cg=args.max_cg, tol_cg_rel=args.tol_cg_rel,
+                           check=False)
         torch.cuda.synchronize()
         single.append({"k": k, "seconds": time.perf_counter() - t0, "mm": s1.mm_iters,
                        "cg": s1.cg_iters, "f": s1.f, "f_batch": sts[k].f, "status": s1.status})
@@ -417,6 +437,60 @@ def serve5(args):
     return out
 
 
+def served_stream_leg(args, dev):
+    """The served mixed stream in the bench line: the first --stream-requests requests
+    of the served-stream recipe (p log-uniform in [500, --p-hi], n = p/4, FP32 or BF16
+    X, chain / lattice / 5-NN, lambdas log-uniform in [1e-3, 1]), inputs generated on
+    the GPU before the clock starts, offered open-loop as Poisson arrivals at
+    --stream-rate requests/s to a --slots-slot server.  Each fit stops at the bench's
+    tol or after --stream-max-mm MM iterations (status 4, reported with its est_err).
+    Latency is submit to result; fits/s is requests / (first submit to last result)."""
+    import threading
+    import torch
+    import flr_inputs as fi
+    import paper_1306_1970_gb300 as flr
+    reqs = fi.served_stream(args.stream_requests, seed=5000, p_lo=500, p_hi=args.p_hi)
+    data = []
+    for r in reqs:
+        X, y, g, _ = fi.request_problem_device(r, dev)
+        if r.dtype == "bf16":
+            X = X.view(torch.int16)
+        data.append((r, X, y, g))
+    torch.cuda.synchronize()
+    srv = flr.Server(slots=args.slots)
+    ids = [None] * len(data)
+    start = time.perf_counter()
+
+    def feeder():
+        for k, (r, X, y, g) in enumerate(data):
+            dt = start + r.arrival / args.stream_rate - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids[k] = srv.submit(X, y, g, r.lam1, r.lam2, eps=1e-6, tol=args.tol,
+                                dtype="bf16" if r.dtype == "bf16" else None, tol_cg=args.tol_cg,
+                                max_mm=args.stream_max_mm, tol_cg_rel=args.tol_cg_rel)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    res = [srv.wait(i)[1] for i in ids]
+    wall = max(rr.t_end for rr in res) - min(rr.t_submit for rr in res)   # server clock
+    srv.close()
+    lat = [rr.t_end - rr.t_submit for rr in res]
+    st = [rr.status for rr in res]
+    capped = [rr.stats.est_err for rr in res if rr.status == 4]
+    return {"requests": len(res), "offered_rate_per_s": args.stream_rate, "slots": args.slots,
+            "p_range": [500, args.p_hi], "fits_per_s": len(res) / wall, "seconds": wall,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "status_ok": int(sum(1 for x in st if x == 0)),
+            "status_max_mm": len(capped), "max_mm": args.stream_max_mm,
+            "est_err_of_capped_max": max(capped) if capped else None,
+            "status_other": int(sum(1 for x in st if x not in (0, 4))),
+            "mm_iters": [rr.stats.mm_iters for rr in res], "p": [r.p for r in reqs],
+            "note": "first requests of the served-stream recipe (seed 5000), open-loop Poisson "
+                    "arrivals; inputs resident on the GPU before the clock starts"}
+
+
 def solve_once(args):
     """One solve of a workload with capped iterations (the unit a profiler captures)."""
     import torch
@@ -428,6 +502,18 @@ def solve_once(args):
         return solve_chain3(args)
     if args.once == "serve5":
         return serve5(args)
+    if args.once == "stream":
+        flr.load(build_if_missing=True)
+        print(json.dumps(served_stream_leg(args, torch.device("cuda", torch.cuda.current_device()))))
+        return
+    if args.once == "hbm4":
+        pr, prob, opts = hbm_problem(args, torch.device("cuda", torch.cuda.current_device()))
+        _, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=args.tol, opts=opts, check=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"once": "hbm4", "n": pr.n, "p": pr.p, "mm_iters": st.mm_iters,
+                          "cg_iters": st.cg_iters, "status": st.status, "ms": st.ms,
+                          "us_per_cg": 1000.0 * st.ms / max(1, st.cg_iters + st.mm_iters)}))
+        return
     flr.load(build_if_missing=True)
     pr = fi.config(2) if args.once == "config2" else fi.config(4)
     X = torch.from_numpy(pr.X).cuda()
@@ -549,6 +635,10 @@ def main():
                   "note": "independent copies of the workload (dataset seeds 1..slots) solved "
                           "concurrently through flr_server; host wall clock from submit to last result"}
 
+    stream_leg = None
+    if args.stream_requests > 0 and rank == 0:
+        stream_leg = served_stream_leg(args, dev)
+
     if rank != 0:
         if pg:
             pg.destroy_process_group()
@@ -565,13 +655,17 @@ def main():
     alg = [algorithmic_bytes(s, pr.n, pr.p, pr.graph.m, bx) for s in stats]
     achieved = sum(alg) / (sum(kern_ms) / 1000.0) / 1e9
     peak, peak_kind = measured_peaks()
-    tr = ncu_traffic()
+    tr = ncu_traffic("config2")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind,
-            "traffic": tr["dram_bytes_per_launch_scaled"] if tr else None,
+            "traffic": tr["dram_bytes_per_launch"] if tr else None,
             "kernel": "mm_solve_kernel<float, stencil>",
             "algorithmic_bytes_per_launch": float(np.mean(alg)),
-            "note": "X (40 MB) stays L2-resident across the CG iterations of one solve"}
+            "note": "X (40 MB) is read from DRAM once per solve and then stays on chip "
+                    "(TMEM and shared memory of the 152 blocks) across its CG iterations: "
+                    "this workload is bound by grid-barrier latency, not by HBM, so the "
+                    "fraction is algorithmic bytes over the HBM peak, not DRAM use; the "
+                    "HBM-streaming case is roofline_hbm_leg"}
     hbm = hbm_leg(args, dev, peak, peak_kind) if args.hbm_mm > 0 else None
     cpu = None
     if not args.no_cpu_baseline:
@@ -599,6 +693,7 @@ def main():
         "roofline_hbm_leg": hbm,
         "cpu_baseline": cpu,
         "served_form": served,
+        "served_stream": stream_leg,
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "wall_s_timed": t_wall,

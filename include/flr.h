@@ -137,8 +137,8 @@ typedef struct flr_opts {
                             the X p and X^T u halves of the product (one-pass Q-apply).
                             -1: every column streamed twice per CG iteration.  1: the
                             one-pass Q-apply at any size (32- and 16-bit X; for tests). */
-    double tol_cg_rel;   /* adaptive inner tolerance (default 0 = off; flr_solve and
-                            flr_solve_noalloc).  With theta = tol_cg_rel > 0, the inner solve
+    double tol_cg_rel;   /* adaptive inner tolerance (default 0 = off; flr_solve,
+                            flr_solve_noalloc and, per RHS, flr_solve_batch).  With theta = tol_cg_rel > 0, the inner solve
                             of MM iteration r stops when ||r|| / ||X^T y|| <= max(tol_cg,
                             min(theta * rel_r, ||r0|| / (2 ||X^T y||))), rel_r the relative
                             change of f that iteration's outer test just measured (1 at r = 0)

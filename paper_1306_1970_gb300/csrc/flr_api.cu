@@ -262,6 +262,13 @@ flr_status launch_solve_t(flr_handle* h, SolveParams& P, int G, size_t smem) {
   FLR_TRY(max_dynamic_smem((const void*)kern, h->device, &dyn_max));
   if (smem > (size_t)dyn_max) return FLR_ENOTIMPL;
   FLR_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+  if (CH) {   // the chunked Q-apply's ring: as many stage slots as fit, at most kRing
+    const size_t roff = ring_offset(smem);
+    const long long ns = roff < (size_t)dyn_max ? ((long long)dyn_max - (long long)roff) / kStage : 0;
+    if (ns < 2) return FLR_ENOTIMPL;
+    P.chunked = (int)(ns < kRing ? ns : kRing);
+    smem = roff + (size_t)P.chunked * kStage;
+  }
   // slab columns after the TMEM ones resident in shared memory (x_smem = 0), the rest streamed
   if (P.ws != 0) {
     P.ws = resident_columns(P.w - P.wt, P.ldn, sizeof(TX), smem, dyn_max);
@@ -279,15 +286,18 @@ flr_status launch_solve_t(flr_handle* h, SolveParams& P, int G, size_t smem) {
 flr_status launch_solve(flr_handle* h, SolveParams& P, int G, size_t smem) {
   const int gk = h->gkind == FLR_E_EDGES ? GK_CSR : GK_STENCIL;
   if (P.chunked) {   // one-pass Q-apply for X larger than L2 (32- and 16-bit X)
+    flr_status s = FLR_EINVAL;
     switch (h->dtype) {
-      case FLR_F32: return gk ? launch_solve_t<float, GK_CSR, true>(h, P, G, smem)
-                              : launch_solve_t<float, GK_STENCIL, true>(h, P, G, smem);
-      case FLR_BF16: return gk ? launch_solve_t<__nv_bfloat16, GK_CSR, true>(h, P, G, smem)
-                               : launch_solve_t<__nv_bfloat16, GK_STENCIL, true>(h, P, G, smem);
-      case FLR_F16: return gk ? launch_solve_t<__half, GK_CSR, true>(h, P, G, smem)
-                              : launch_solve_t<__half, GK_STENCIL, true>(h, P, G, smem);
+      case FLR_F32: s = gk ? launch_solve_t<float, GK_CSR, true>(h, P, G, smem)
+                           : launch_solve_t<float, GK_STENCIL, true>(h, P, G, smem); break;
+      case FLR_BF16: s = gk ? launch_solve_t<__nv_bfloat16, GK_CSR, true>(h, P, G, smem)
+                            : launch_solve_t<__nv_bfloat16, GK_STENCIL, true>(h, P, G, smem); break;
+      case FLR_F16: s = gk ? launch_solve_t<__half, GK_CSR, true>(h, P, G, smem)
+                           : launch_solve_t<__half, GK_STENCIL, true>(h, P, G, smem); break;
+      default: break;
     }
-    return FLR_EINVAL;
+    if (s != FLR_ENOTIMPL) return s;
+    P.chunked = 0;   // no room for two ring slots: every column streamed twice instead
   }
   switch (h->dtype) {
     case FLR_F64: return gk ? launch_solve_t<double, GK_CSR>(h, P, G, smem)
@@ -366,6 +376,7 @@ flr_status batch_group(flr_handle* h, int K, const double* l1, const double* l2,
   P.y = h->y; P.c = h->c; P.d = h->d; P.cnorm = h->cnorm > 0 ? h->cnorm : 1.0;
   P.lam1 = h->blam; P.lam2 = h->blam + kNRMax;
   P.eps = eps; P.tol = tol; P.tol_cg = o.tol_cg > 0.0 ? o.tol_cg : tol;
+  P.tol_cg_rel = o.tol_cg_rel;
   P.max_mm = o.max_mm; P.max_cg = o.max_cg; P.min_cg = o.min_cg;
   P.S = h->bS; P.kchunk = h->bkchunk;
   double** v = h->bvec;
@@ -769,7 +780,7 @@ flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const doub
   flr_default_opts(&o);
   if (opts) o = *opts;
   if (o.max_mm < 0 || o.max_cg < 0 || o.min_cg < 0 || o.tol_cg < 0.0 || o.wait_cycles < 0 ||
-      o.max_refine < 0)
+      o.max_refine < 0 || !(o.tol_cg_rel >= 0.0))
     return FLR_EINVAL;
   DeviceGuard dg(h->device);
   // tensor-core multi-RHS path: BF16 X, chain/lattice, a diagonal or per-tile tridiagonal preconditioner

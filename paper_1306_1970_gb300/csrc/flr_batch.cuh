@@ -50,6 +50,7 @@ struct BatchParams {
   const double* lam1;          // K values (device)
   const double* lam2;
   double eps, tol, tol_cg;
+  double tol_cg_rel;           // adaptive inner tolerance factor (0 = off)
   int max_mm, max_cg, min_cg;
   int precond;                 // PC_JACOBI, PC_TRIDIAG or PC_PAPER
   int max_refine;              // FP64 residual restarts of each RHS's inner solve per MM iteration
@@ -306,6 +307,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
   double* s_relres = scal + 8 * kNRMax; double* s_pen = scal + 9 * kNRMax;   // 2 * kNRMax
   double* s_psp = scal + 11 * kNRMax;  double* s_uu = scal + 12 * kNRMax;
   double* s_relp = scal + 13 * kNRMax;
+  double* s_tin = scal + 20 * kNRMax;  // inner tolerance of each RHS's current CG cycle
   int* s_act = reinterpret_cast<int*>(scal + 14 * kNRMax);      // MM-active
   int* s_cga = s_act + kNRMax;                                     // CG-active
   int* s_mm = s_act + 2 * kNRMax;
@@ -601,12 +603,18 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
     if (tid < kNRMax) {
       const int k = tid;
       int go = (k < K && set[k] && s_act[k]) ? 1 : 0;
+      const double rel_r = go ? sqrt(s_rr[k]) / P.cnorm : 0.0;
       if (refining && go) {   // the true residual decides whether CG restarts
         ++s_nref[k];
         ++s_nreft[k];
-        const double rel_r = sqrt(s_rr[k]) / P.cnorm;
         s_relres[k] = rel_r;
-        if (rel_r <= P.tol_cg) go = 0;
+        if (rel_r <= s_tin[k]) go = 0;
+      }
+      // the cycle's inner tolerance: tol_cg, or with tol_cg_rel = theta > 0,
+      // max(tol_cg, min(theta * rel_change, ||r0|| / (2 ||c||))) as in flr_solve
+      if (go) {
+        const double ad = P.tol_cg_rel * (s_mm[k] > 0 ? s_rel[k] : 1.0);
+        s_tin[k] = P.tol_cg_rel > 0.0 ? fmax(P.tol_cg, fmin(ad, 0.5 * rel_r)) : P.tol_cg;
       }
       s_cga[k] = go;
       s_cgr[k] = 0;
@@ -620,7 +628,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         if (s_cga[k]) {
           const double rel_r = sqrt(s_rr[k]) / P.cnorm;
           s_relres[k] = rel_r;
-          if (kcg >= P.max_cg || (kcg >= P.min_cg && rel_r <= P.tol_cg)) s_cga[k] = 0;
+          if (kcg >= P.max_cg || (kcg >= P.min_cg && rel_r <= s_tin[k])) s_cga[k] = 0;
           else { s_cg[k] += 1; s_cgr[k] += 1; }
         }
       }

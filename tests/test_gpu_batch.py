@@ -49,6 +49,26 @@ def test_batch_chain_bf16_matches_oracle(flr, K):
         assert abs(sts[k].f_eps - fe) <= 1e-9 * abs(fe)
 
 
+def test_batch_adaptive_inner_tolerance_matches_oracle(flr):
+    """tol_cg_rel = 1 per RHS: loose early surrogate solves, tol_cg late ones.  The
+    fixed point is the same, so the converged results meet the same gates."""
+    pr = fi.config(3, scale=0.01)
+    grid = pr.lam_grid[[0, 9, 36, 63]]
+    prob = bf16_problem(flr, pr)
+    betas, objs, sts = prob.solve_batch(grid[:, 0], grid[:, 1], eps=pr.eps, tol=1e-12,
+                                        tol_cg=1e-10, tol_cg_rel=1.0, max_mm=20000)
+    X64 = pr.X64()
+    for k, (l1, l2) in enumerate(grid):
+        ref = mm.mm_dense(X64, pr.y, pr.graph.edges, l1, l2, pr.eps, tol=1e-13)
+        assert sts[k].status == 0, sts[k]
+        gap = abs(sts[k].f - ref.f) / abs(ref.f)
+        b = betas[:, k].cpu().numpy()
+        db = np.abs(b - ref.beta).max() / max(np.abs(ref.beta).max(), 1e-300)
+        print(f"k={k} gap={gap:.2e} dbeta={db:.2e} mm={sts[k].mm_iters} cg={sts[k].cg_iters}")
+        assert gap <= 1e-6, (k, l1, l2, gap, sts[k])
+        assert db <= 1e-4, (k, l1, l2, db)
+
+
 def test_batch_lattice_bf16_matches_single_solves(flr):
     pr = fi.config(2, scale=0.04)          # 20x20 lattice, n=40 (quantised to BF16 here)
     Xs, Xw = fi.quantize(pr.X64(), "bf16")

@@ -197,15 +197,26 @@ def test_config4_q50x80_against_oracle(flr):
     assert_iterate(flr, prob, pr, golden("config4_q50x80_r300"))
 
 
-@pytest.mark.parametrize("x_smem", [1, -1])
-def test_q_apply_variants_match_oracle(flr, x_smem):
+@pytest.mark.parametrize("x_smem,grid", [(1, 0), (1, 16), (-1, 0)])
+def test_q_apply_variants_match_oracle(flr, x_smem, grid):
     """The one-pass chunked Q-apply (x_smem = 1: X read once per CG iteration in row
-    chunks of 128, the last one ragged at n = 200) and the two-pass streamed one
-    (x_smem = -1) both give the oracle's MM iterates (50 x 80 lattice, FP16)."""
+    chunks of 128, the last one ragged at n = 200; with 16 blocks a block's 250
+    columns make 8 stages of 32 columns per chunk, the last one ragged) and the
+    two-pass streamed one (x_smem = -1) both give the oracle's MM iterates
+    (50 x 80 lattice, FP16)."""
     g = golden("config4_q50x80_r300")
     pr = fi.config(4, scale=0.04)
     prob = problem(flr, pr)
-    assert_iterate(flr, prob, pr, g, x_smem=x_smem)
+    assert_iterate(flr, prob, pr, g, x_smem=x_smem, grid=grid)
+
+
+def test_chunked_q_apply_f32_matches_oracle(flr):
+    """The one-pass chunked Q-apply on FP32 X (row chunks of 64: n = 160 gives 3
+    chunks, the last ragged; 24 blocks of 67 columns give 3 stages per chunk) gives
+    the oracle's iterates on the 40 x 40 lattice."""
+    pr = fi.config(2, scale=0.16)
+    prob = problem(flr, pr)
+    assert_iterate(flr, prob, pr, golden("config2_q40_r300"), x_smem=1, grid=24)
 
 
 def test_config4_full_size_is_stationary(flr):
@@ -246,8 +257,10 @@ def test_bf16_chain_against_inline_oracle(flr):
 def test_config2_full_size(flr):
     """The bench workload (q=100 lattice, n=1000, FP32) against the oracle: the
     objective gap at the bench's own stop settings (tol 1e-9, tol_cg 1e-8, no
-    refinement restarts), and every coefficient of the MM iterate after 200
-    iterations at 1e-4 of max |beta|."""
+    refinement restarts); every coefficient of the MM iterate after 200
+    iterations at 1e-4 of max |beta|; and every coefficient of the limit at
+    1e-4 of max |beta| when the GPU runs the exact MM map to the oracle's stop
+    (relative change of f below 1e-13)."""
     g = golden("config2")
     pr = fi.config(2)
     check_fingerprint(pr, g)
@@ -257,6 +270,10 @@ def test_config2_full_size(flr):
     assert st.status == 0 and gap <= GAP, (gap, st)
     assert st.est_err >= gap, (st.est_err, gap)
     assert_iterate(flr, prob, pr, golden("config2_r200"))
+    beta, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=1e-13, max_mm=20000, **EXACT)
+    assert_parity(st, beta, g["f"], np.array(g["beta"]))
+    db = np.abs(beta.cpu().numpy() - np.array(g["beta"])).max() / np.abs(np.array(g["beta"])).max()
+    print(f"limit: mm={st.mm_iters} (oracle {g['iters']}), max|dbeta|/|beta|inf = {db:.2e}")
 
 
 @pytest.mark.parametrize("p", [1000, 10000])
