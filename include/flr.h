@@ -129,14 +129,16 @@ typedef struct flr_opts {
                             the iterates follow the MM map of Algorithm 1 (mixed-precision
                             iterative refinement).  flr_solve_batch applies it per RHS. */
     int32_t x_smem;      /* where the X products read X (flr_solve; flr_solve_noalloc takes 0
-                            or -1).  0 (default): when X fits in L2 (<= 96 MB), the leading
-                            columns of each thread block's slab stay on chip for the whole
-                            solve, in tensor memory (TMEM, 32- and 16-bit X, n <= 2048) and
-                            then in shared memory, the rest streamed; when X is larger, each
-                            CG iteration reads X once in row chunks that stay in L2 between
-                            the X p and X^T u halves of the product (one-pass Q-apply).
+                            or -1).  0 (default): the leading columns of each thread block's
+                            slab stay on chip for the whole solve, in tensor memory (TMEM,
+                            32- and 16-bit X, n <= 2048) and then in shared memory; the
+                            rest are streamed, twice per CG iteration (X p, then X^T u).
                             -1: every column streamed twice per CG iteration.  1: the
-                            one-pass Q-apply at any size (32- and 16-bit X; for tests). */
+                            one-pass Q-apply (32- and 16-bit X): each CG iteration reads X
+                            once from memory in row chunks that stay in L2 between the X p
+                            and X^T u halves of the product, with a grid-wide split barrier
+                            per chunk; on GB300 it is slower than two passes at every
+                            measured size, so it is never chosen by default. */
     double tol_cg_rel;   /* adaptive inner tolerance (default 0 = off; flr_solve,
                             flr_solve_noalloc and, per RHS, flr_solve_batch).  With theta = tol_cg_rel > 0, the inner solve
                             of MM iteration r stops when ||r|| / ||X^T y|| <= max(tol_cg,
@@ -309,13 +311,18 @@ flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n, int64_t p
  * Requests (X, y, E, lambdas) are queued by flr_server_submit.  `slots`
  * worker threads each own a CUDA stream; a free worker admits the oldest
  * queued request whose device-memory footprint fits in what is left of
- * `hbm_budget`, creates its handle on the slot's stream, solves it with at
- * most `grid_per_slot` thread blocks, copies beta to the server and frees
- * the handle.  Requests that arrive while others run are admitted as slots
- * and memory free up, and their kernels run concurrently on the device
- * (slots * grid_per_slot <= number of SMs keeps every cooperative solve
- * co-resident).  A request's X, y and edges are borrowed: they must stay
- * valid until flr_server_wait has returned for it.
+ * `hbm_budget`, creates its handle on the slot's stream (or reuses the slot's
+ * resident handle for the same data_id), solves it with at most
+ * `grid_per_slot` thread blocks, copies beta to the server and frees (or
+ * keeps) the handle.  Requests that arrive while others run are admitted as
+ * slots and memory free up, and their kernels run concurrently on the device.
+ * The server's solves hold at most slots * grid_per_slot (<= number of SMs)
+ * thread blocks at once, one per SM, which keeps every cooperative solve
+ * co-resident: a problem too wide for grid_per_slot blocks (each block's
+ * slab of coefficients must fit its shared-memory vectors) takes as many
+ * blocks as it needs from that budget, waiting in arrival order until they
+ * are free.  A request's X, y and edges are borrowed: they must stay valid
+ * until flr_server_wait has returned for it.
  * ------------------------------------------------------------------------- */
 typedef struct flr_server flr_server;
 typedef flr_server* flr_server_t;

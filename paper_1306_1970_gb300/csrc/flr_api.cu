@@ -262,13 +262,6 @@ flr_status launch_solve_t(flr_handle* h, SolveParams& P, int G, size_t smem) {
   FLR_TRY(max_dynamic_smem((const void*)kern, h->device, &dyn_max));
   if (smem > (size_t)dyn_max) return FLR_ENOTIMPL;
   FLR_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
-  if (CH) {   // the chunked Q-apply's ring: as many stage slots as fit, at most kRing
-    const size_t roff = ring_offset(smem);
-    const long long ns = roff < (size_t)dyn_max ? ((long long)dyn_max - (long long)roff) / kStage : 0;
-    if (ns < 2) return FLR_ENOTIMPL;
-    P.chunked = (int)(ns < kRing ? ns : kRing);
-    smem = roff + (size_t)P.chunked * kStage;
-  }
   // slab columns after the TMEM ones resident in shared memory (x_smem = 0), the rest streamed
   if (P.ws != 0) {
     P.ws = resident_columns(P.w - P.wt, P.ldn, sizeof(TX), smem, dyn_max);
@@ -285,7 +278,7 @@ flr_status launch_solve_t(flr_handle* h, SolveParams& P, int G, size_t smem) {
 
 flr_status launch_solve(flr_handle* h, SolveParams& P, int G, size_t smem) {
   const int gk = h->gkind == FLR_E_EDGES ? GK_CSR : GK_STENCIL;
-  if (P.chunked) {   // one-pass Q-apply for X larger than L2 (32- and 16-bit X)
+  if (P.chunked) {   // one-pass chunked Q-apply (32- and 16-bit X)
     flr_status s = FLR_EINVAL;
     switch (h->dtype) {
       case FLR_F32: s = gk ? launch_solve_t<float, GK_CSR, true>(h, P, G, smem)
@@ -296,8 +289,7 @@ flr_status launch_solve(flr_handle* h, SolveParams& P, int G, size_t smem) {
                            : launch_solve_t<__half, GK_STENCIL, true>(h, P, G, smem); break;
       default: break;
     }
-    if (s != FLR_ENOTIMPL) return s;
-    P.chunked = 0;   // no room for two ring slots: every column streamed twice instead
+    return s;
   }
   switch (h->dtype) {
     case FLR_F64: return gk ? launch_solve_t<double, GK_CSR>(h, P, G, smem)
@@ -677,11 +669,9 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
   const int V = ident ? XT<IdX>::V : (int)(16 / dtype_size(h->dtype));
   const long long q2p = h->gkind == FLR_E_LATTICE ? h->q2 : h->p;
   // X on chip (x_smem = 0): the leading columns of every slab in TMEM, the next
-  // ones in shared memory (sized at launch), the rest streamed
-  // X larger than L2: the chunked one-pass Q-apply instead (32- and 16-bit X)
-  const bool chunked = !ident && h->dtype != FLR_F64 &&
-                       ((o.x_smem == 0 && use_chunked(h->n, h->p, (int)dtype_size(h->dtype))) ||
-                        o.x_smem == 1);
+  // ones in shared memory (sized at launch), the rest streamed twice per CG
+  // iteration; x_smem = 1: the chunked one-pass Q-apply (32- and 16-bit X)
+  const bool chunked = !ident && h->dtype != FLR_F64 && o.x_smem == 1;
   const int tct = (o.x_smem == 0 && !ident && !chunked) ? tmem_cells(h->n, (int)dtype_size(h->dtype)) : 0;
   const long long trows = tct > 0 ? (h->n + 127) / 128 * 128 : 0;
   const size_t smem = solve_smem_bytes(h->ldn, wpad, V, halo_entries(wpad, q2p, h->p), trows);
@@ -815,6 +805,28 @@ flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const doub
 void flr_destroy(flr_t h) { release(h); }
 
 }  // extern "C"
+
+int flr_min_grid(flr_t h) {
+  if (!h || h->dtype == FLR_IDENTITY) return 1;
+  int dyn_max = 0;
+  if (max_dynamic_smem((const void*)mm_solve_kernel<float, GK_STENCIL>, h->device, &dyn_max) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return -1;
+  }
+  const int V = (int)(16 / dtype_size(h->dtype));
+  const long long q2p = h->gkind == FLR_E_LATTICE ? h->q2 : h->p;
+  // as flr_solve with the default x_smem: TMEM row partials when X fits in TMEM
+  const int tct = h->dtype != FLR_F64 ? tmem_cells(h->n, (int)dtype_size(h->dtype)) : 0;
+  const long long trows = tct > 0 ? (h->n + 127) / 128 * 128 : 0;
+  for (long long G = 1; G <= h->sm_count && G <= kMaxGrid; ++G) {
+    const long long w = (h->p + G - 1) / G;
+    if (w > 8192) continue;
+    const long long wpad = (w + 3) / 4 * 4;
+    if (solve_smem_bytes(h->ldn, wpad, V, halo_entries(wpad, q2p, h->p), trows) <= (size_t)dyn_max)
+      return (int)G;
+  }
+  return -1;
+}
 
 void flr_kernel_span(flr_t h, unsigned long long* t0, unsigned long long* t1) {
   *t0 = h ? h->span_t0 : 0;

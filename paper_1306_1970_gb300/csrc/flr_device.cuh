@@ -27,12 +27,6 @@ __device__ __forceinline__ uint64_t l2_keep_policy() {
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   return pol;
 }
-// Lines read for the last time: evicted first.
-__device__ __forceinline__ uint64_t l2_drop_policy() {
-  uint64_t pol;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
 __device__ __forceinline__ uint4 ld_stream16(const void* p) {
   uint4 r;
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"

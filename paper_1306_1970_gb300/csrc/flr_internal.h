@@ -4,6 +4,10 @@
 
 #include "../../include/flr.h"
 
+// Fewest thread blocks flr_solve can run handle h's problem on: a block's slab
+// of the p coefficients must fit its shared-memory vectors (-1 if none does).
+int flr_min_grid(flr_t h);
+
 // Global-timer span (ns) of the last solve kernel run on handle h (0, 0 if none).
 void flr_kernel_span(flr_t h, unsigned long long* t0, unsigned long long* t1);
 

@@ -49,6 +49,11 @@ struct flr_server {
   std::unordered_map<uint64_t, Done> done;
   std::unordered_map<uint64_t, bool> pending;   // submitted, not yet finished
   int64_t in_use = 0;
+  // thread blocks of the device the server's cooperative solves may hold at once
+  // (slots x grid_per_slot <= #SMs, one block per SM): taken in ticket order
+  int blocks_free = 0, blocks_total = 0;
+  uint64_t ticket_next = 0, ticket_serving = 0;
+  std::condition_variable cv_blocks;
   uint64_t next_id = 1;
   bool stopping = false;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
@@ -159,12 +164,33 @@ void flr_server::worker(int slot) {
       flr_opts op;
       flr_default_opts(&op);
       if (r.use_opts) op = r.opts;
-      // the solve kernel's own sizing rule, capped at the slot's share of the SMs
+      // the solve kernel's own sizing rule, capped at the slot's share of the SMs;
+      // a problem whose slabs need more blocks than that (their vectors must fit
+      // in shared memory) takes more of the server's blocks, waiting for them
       const long long per_block = r.dtype == FLR_F64 ? 8192 : 65536;
       long long g = op.grid > 0 ? op.grid : (r.n * r.p + per_block - 1) / per_block;
-      op.grid = (int32_t)std::max<long long>(1, std::min<long long>(g, o.grid_per_slot));
-      st = flr_solve(h, r.lambda1, r.lambda2, r.eps, r.tol, &op, nullptr, d.beta.data(), FLR_MEM_HOST,
-                     &d.res.stats);
+      g = std::max<long long>(1, std::min<long long>(g, o.grid_per_slot));
+      const int gmin = flr_min_grid(h);
+      if (gmin > g) g = gmin;
+      op.grid = (int32_t)g;
+      // blocks held: a solve wider than the server's whole share runs alone
+      const int need = (int)std::min<long long>(g, blocks_total);
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        const uint64_t t = ticket_next++;
+        cv_blocks.wait(lk, [&] { return ticket_serving == t && blocks_free >= need; });
+        blocks_free -= need;
+        ++ticket_serving;
+      }
+      cv_blocks.notify_all();
+      st = gmin < 0 ? FLR_ENOTIMPL
+                    : flr_solve(h, r.lambda1, r.lambda2, r.eps, r.tol, &op, nullptr, d.beta.data(),
+                                FLR_MEM_HOST, &d.res.stats);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        blocks_free += need;
+      }
+      cv_blocks.notify_all();
       unsigned long long t0 = 0, t1 = 0;
       flr_kernel_span(h, &t0, &t1);
       d.res.dev_t0_ns = t0;
@@ -210,6 +236,7 @@ extern "C" flr_status flr_server_create(const flr_server_opts* opts, flr_server_
     delete s;   // cooperative solves must all fit on the device at once
     return FLR_EINVAL;
   }
+  s->blocks_total = s->blocks_free = s->o.slots * s->o.grid_per_slot;
   for (int i = 0; i < s->o.slots; ++i) {
     cudaStream_t st = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {

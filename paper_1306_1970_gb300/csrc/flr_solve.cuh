@@ -90,23 +90,12 @@ constexpr double kStrong = 16.0;   // strong-edge threshold of PC_TWOLEVEL
 constexpr int kRF = 3;   // fields per block reduction
 constexpr int kLA = 16;  // 16-byte X loads in flight per thread in phase A
 // One-pass (chunked) Q-apply for X larger than L2: row chunks of kCRV 16-byte
-// row vectors; stages of kSC column segments (kSeg bytes each) staged through a
-// ring of at most kRing shared-memory slots by bulk asynchronous copies.
+// row vectors, kCCG column groups.
 constexpr int kCRV = 16;
-constexpr int kCCG = kThreads / kCRV;   // column lanes of a thread block (16)
-constexpr int kSC = 32;                 // columns per stage (one copy per lane of warp 0)
-constexpr int kSeg = kCRV * 16;         // bytes of one column segment of a chunk
-constexpr int kStage = kSC * kSeg;      // bytes of one ring slot
-constexpr int kRing = 8;                // most ring slots
-static_assert(kSC == 2 * kCCG, "each thread takes two columns of a stage");
-static_assert(kCRV <= 32 && kSC <= 32, "a chunk's row vectors share a warp; one copy per lane of warp 0");
-// the ring starts at the first 128-byte boundary after the kernel's other shared memory
-__host__ __device__ inline size_t ring_offset(size_t base) { return ((base + 15) / 16 * 16 + 127) / 128 * 128; }
+constexpr int kCCG = kThreads / kCRV;
+constexpr int kLC = 8;    // loads in flight per thread in the chunked phase A
+constexpr int kLCC = 8;   // and in the chunked phase C (a power of two <= kCRV)
 
-// The chunked Q-apply is used when X does not fit in L2 (more than 96 MB).
-__host__ __device__ inline bool use_chunked(long long n, long long p, int es) {
-  return (double)n * (double)p * es > 96.0e6;
-}
 constexpr int kUR = 1;   // replicas of each u accumulator: block b adds into replica b % kUR,
                          // spreading the atomics of X p over kUR times more L2 lines
 
@@ -127,7 +116,7 @@ struct SolveParams {
   int ws;                    // slab columns kept in shared memory (after the TMEM ones)
   int wt;                    // leading slab columns kept in TMEM (0 = none)
   int tct;                   // TMEM cells per 128-row group (0 = no TMEM)
-  int chunked;               // one-pass chunked Q-apply: its ring slots (0 = off)
+  int chunked;               // one-pass chunked Q-apply (x_smem = 1)
   unsigned* cbar;            // its two split-barrier counters (128 bytes apart)
   long long w, wpad;         // coefficients per block, padded to a multiple of 4
   int levels;                // PCR levels for the block chunk
@@ -872,24 +861,6 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
                    (P.precond == PC_TRIDIAG || P.precond == PC_PAPER || (two && P.q2 >= P.p));
   const int lane = tid & 31, warp = tid >> 5;
 
-  // ---- chunked Q-apply: ring of P.chunked stage slots after the other shared
-  // memory, one mbarrier per slot.  rs0 is the slot of the next Q-apply's first
-  // stage; bit s of rph the phase parity slot s waits for next.
-  __shared__ __align__(8) uint64_t rfull[kRing];
-  unsigned char* ring = smraw + ring_offset(solve_smem_bytes(P.ldn, wp, V, nh, trows));
-  int rs0 = 0;
-  unsigned rph = 0u;
-  uint64_t pol_keep = 0, pol_drop = 0;
-  if constexpr (CH) {
-    pol_keep = l2_keep_policy();
-    pol_drop = l2_drop_policy();
-    if (tid == 0) {
-      for (int s2 = 0; s2 < P.chunked; ++s2) tc::mbar_init(&rfull[s2], 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-  }
-
   // ---- the slab's first wt columns into TMEM, the next ws into shared memory
   if constexpr (sizeof(TX) == 4 || sizeof(TX) == 2) {
     if (P.tct > 0) tmem_fill<TX>(tmem, Xt, j0, P.wt < wl ? P.wt : wl, n, P.ldn, P.tct);
@@ -1250,159 +1221,131 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
         bool tv_done = false;   // the chunked Q-apply leaves X^T u in tv
         if constexpr (!IDX) {
           if constexpr (CH) {
-            // One pass over X.  The block's slab is cut into row chunks of Rc rows
-            // and column groups of kSC columns; a stage is one (chunk, group) tile,
-            // copied into a ring slot by kSC bulk asynchronous copies (one column
-            // segment each, completing on the slot's mbarrier), so that up to
-            // P.chunked stages are in flight without registers.  Stages run in the
-            // order A(0), A(1), C(0), A(2), C(1), ...: A(s) accumulates X p over
-            // chunk s's rows (X from HBM, kept in L2) and adds it into u; C(s), after
-            // the split barrier of chunk s, re-reads chunk s (from L2, read for the
-            // last time) for X^T u.  Thread (rv, cgl) owns row vector rv of a chunk
-            // and columns cgl, cgl + kCCG of a group.  p^T S p rides on the barrier
-            // of chunk 0.
+            // One pass over X: for row chunk s, phase A of chunk s streams from
+            // HBM and adds into u; after the split barrier of chunk s - 1 (whose
+            // wait overlaps the streaming), phase C of chunk s - 1 re-reads that
+            // chunk from L2.  Each thread owns row vector rv of every chunk and the
+            // slab columns cg, cg + kCCG, ....  p^T S p rides on the barrier of
+            // chunk 0.
             constexpr int Rc = kCRV * V;
-            const int rv = tid % kCRV, cgl = tid / kCRV;
+            const int rv = tid % kCRV, cg = tid / kCRV;
+            const int ncols = wl > cg ? (wl - cg + kCCG - 1) / kCCG : 0;
             const int nch = (int)((n + Rc - 1) / Rc);
-            const int ngr = wl > 0 ? (wl + kSC - 1) / kSC : 1;
-            const int nst = 2 * nch * ngr;
-            const int NSR = P.chunked;
             Acc* red_c = red;
             zero_u(Unext);
-            for (int jj = tid; jj < wl; jj += kThreads) tv[jj] = 0.0;
+            if (tid == 0) P.part[((long long)slot * kNF) * G + b] = 0.0;
             {
               double sv1[1] = {sv[0]};
               block_reduce<1>(sv1, rs, ncol);
               if (tid == 0) P.part[((long long)slot * kNF) * G + b] = sv1[0];
             }
-            // stage c -> chunk ch, group g; true for a C stage
-            auto decode = [&](int c, int& ch, int& g) -> bool {
-              if (c < ngr) { ch = 0; g = c; return false; }
-              const int c2 = c - ngr, r = c2 / (2 * ngr) + 1, rem = c2 % (2 * ngr);
-              if (r < nch && rem < ngr) { ch = r; g = rem; return false; }
-              ch = r - 1;
-              g = r < nch ? rem - ngr : rem;
-              return true;
-            };
-            auto issue = [&](int c) {   // by warp 0
-              int ch, g;
-              const bool isC = decode(c, ch, g);
-              const int sl = (rs0 + c) % NSR;
-              const int left = wl - g * kSC;
-              const int nc = left < 0 ? 0 : (left < kSC ? left : kSC);
-              const long long r0 = (long long)ch * Rc;
-              const long long rows = P.ldn - r0 < Rc ? P.ldn - r0 : Rc;
-              const uint32_t segb = (uint32_t)(rows * (long long)sizeof(TX));   // a multiple of 16
-              if (lane == 0) tc::mbar_expect_tx(&rfull[sl], segb * (uint32_t)nc);
-              __syncwarp();
-              if (lane < nc)
-                tc::bulk_g2s(ring + (size_t)sl * kStage + (size_t)lane * kSeg,
-                             Xt + (j0 + (long long)g * kSC + lane) * P.ldn + r0, segb, &rfull[sl],
-                             isC ? pol_drop : pol_keep);
-            };
-            if (warp == 0)
-              for (int c = 0; c < (nst < NSR ? nst : NSR); ++c) issue(c);
-            Acc acc[V], ul[V];
-#pragma unroll
-            for (int e = 0; e < V; ++e) { acc[e] = Acc(0); ul[e] = Acc(0); }
+            // X^T u accumulates in tv: after each chunk, a column's partials are
+            // summed over the kCRV row-vector lanes by shuffles (the two column
+            // groups of a warp loop to the larger count; lanes past their own
+            // count add zeros) and lane rv == 0 adds the sum to tv.
+            const int ncols_w = wl > (cg & ~1) ? (wl - (cg & ~1) + kCCG - 1) / kCCG : 0;
+            if (rv == 0)
+              for (int c = 0; c < ncols; ++c) tv[cg + c * kCCG] = 0.0;
             double uu_loc = 0.0;
+            auto colptr = [&](int c, long long off) { return Xt + (j0 + cg + (long long)c * kCCG) * P.ldn + off; };
             bool ok = true;
-            int c = 0;
-            for (; c < nst; ++c) {
-              int ch, g;
-              const bool isC = decode(c, ch, g);
-              const int sl = (rs0 + c) % NSR;
-              const long long off = (long long)(ch * kCRV + rv) * V;   // this thread's first row
-              const bool rowok = off < P.ldn;
-              if (isC && g == 0) {   // chunk ch's u is complete after its split barrier
-                if (!sb.wait(ch)) { ok = false; break; }
-                if (ch == 0) {       // p^T S p from the partials published before barrier 0
+            for (int st = 0; st <= nch && ok; ++st) {
+              if (st < nch) {   // phase A of chunk st
+                const long long off = (long long)(st * kCRV + rv) * V;
+                const bool rowok = off < P.ldn;
+                Acc acc[V];
+#pragma unroll
+                for (int e = 0; e < V; ++e) acc[e] = Acc(0);
+#pragma unroll 1
+                for (int c0 = 0; c0 < ncols; c0 += kLC) {
+                  uint4 raw[kLC];
+#pragma unroll
+                  for (int k = 0; k < kLC; ++k)
+                    if (c0 + k < ncols && rowok) raw[k] = ld_stream16(colptr(c0 + k, off));
+#pragma unroll
+                  for (int k = 0; k < kLC; ++k) {
+                    if (c0 + k < ncols && rowok) {
+                      Acc xv[V];
+                      cvt_to<TX, Acc>(raw[k], xv);
+                      const Acc sp = vs[cg + (c0 + k) * kCCG];
+#pragma unroll
+                      for (int e = 0; e < V; ++e) acc[e] = fma(xv[e], sp, acc[e]);
+                    }
+                  }
+                }
+#pragma unroll
+                for (int e = 0; e < V; ++e) red_c[cg * Rc + rv * V + e] = acc[e];
+                __syncthreads();
+                for (int i = tid; i < Rc; i += kThreads) {
+                  Acc sum = Acc(0);
+                  for (int g = 0; g < kCCG; ++g) sum += red_c[g * Rc + i];
+                  const long long row = (long long)st * Rc + i;
+                  if (row < n && sum != Acc(0)) atomicAdd(Ucur + row, sum);
+                }
+                sb.arrive(st);
+              }
+              if (st > 0) {     // phase C of chunk st - 1
+                if (!sb.wait(st - 1)) { ok = false; break; }
+                if (st == 1) {  // p^T S p from the partials published before barrier 0
                   double v1[1] = {tid < G ? ldcg(&P.part[((long long)slot * kNF) * G + tid]) : 0.0};
                   block_reduce<1>(v1, rs, G);
                   sv[0] = v1[0];
                 }
+                const long long off = (long long)((st - 1) * kCRV + rv) * V;
+                const bool rowok = off < P.ldn;
+                Acc ul[V];
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
                   const long long row = off + e;
                   ul[e] = (rowok && row < n) ? ldcg(Ucur + row) : Acc(0);
-                  if (cgl == 0) uu_loc = fma((double)ul[e], (double)ul[e], uu_loc);
+                  if (cg == 0) uu_loc = fma((double)ul[e], (double)ul[e], uu_loc);
+                }
+#pragma unroll 1
+                for (int c0 = 0; c0 < ncols_w; c0 += kLCC) {
+                  uint4 raw[kLCC];
+#pragma unroll
+                  for (int k = 0; k < kLCC; ++k)
+                    if (c0 + k < ncols && rowok) raw[k] = ld_stream16(colptr(c0 + k, off));
+                  Acc d[kLCC];
+#pragma unroll
+                  for (int k = 0; k < kLCC; ++k) {
+                    d[k] = Acc(0);
+                    if (c0 + k < ncols && rowok) {
+                      Acc xv[V];
+                      cvt_to<TX, Acc>(raw[k], xv);
+#pragma unroll
+                      for (int e = 0; e < V; ++e) d[k] = fma(xv[e], ul[e], d[k]);
+                    }
+                  }
+                  // reduce-scatter over the kCRV lanes: each halving step keeps the
+                  // upper or lower half of the columns, then the remaining lanes of
+                  // a group all-reduce; lane rv ends with column col
+                  int col = 0;
+                  int m = kLCC;
+#pragma unroll
+                  for (int o = kCRV / 2; o >= 1; o >>= 1) {
+                    if (m > 1) {
+                      const bool hi = (rv & o) != 0;
+#pragma unroll
+                      for (int i = 0; i < kLCC / 2; ++i) {
+                        if (i < m / 2) {
+                          const Acc send = hi ? d[i] : d[i + m / 2];
+                          const Acc keep = hi ? d[i + m / 2] : d[i];
+                          d[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                        }
+                      }
+                      if (hi) col += m / 2;
+                      m /= 2;
+                    } else {
+                      d[0] += __shfl_xor_sync(0xffffffffu, d[0], o);
+                    }
+                  }
+                  if ((rv & (kCRV / kLCC - 1)) == 0 && c0 + col < ncols)
+                    tv[cg + (c0 + col) * kCCG] += (double)d[0];
                 }
               }
-              if (!tc::mbar_wait(&rfull[sl], (rph >> sl) & 1u, P.timeout)) ok = false;
-              const unsigned char* stg = ring + (size_t)sl * kStage + (size_t)rv * 16;
-              const int cl0 = g * kSC + cgl, cl1 = cl0 + kCCG;   // slab columns of this thread
-              if (!isC) {
-                if (rowok) {
-                  if (cl0 < wl) {
-                    Acc xv[V];
-                    cvt_to<TX, Acc>(*reinterpret_cast<const uint4*>(stg + (size_t)cgl * kSeg), xv);
-                    const Acc sp = vs[cl0];
-#pragma unroll
-                    for (int e = 0; e < V; ++e) acc[e] = fma(xv[e], sp, acc[e]);
-                  }
-                  if (cl1 < wl) {
-                    Acc xv[V];
-                    cvt_to<TX, Acc>(*reinterpret_cast<const uint4*>(stg + (size_t)(cgl + kCCG) * kSeg), xv);
-                    const Acc sp = vs[cl1];
-#pragma unroll
-                    for (int e = 0; e < V; ++e) acc[e] = fma(xv[e], sp, acc[e]);
-                  }
-                }
-                if (g == ngr - 1) {   // chunk ch done: sum over the column lanes, add into u
-#pragma unroll
-                  for (int e = 0; e < V; ++e) { red_c[cgl * Rc + rv * V + e] = acc[e]; acc[e] = Acc(0); }
-                  __syncthreads();
-                  for (int i = tid; i < Rc; i += kThreads) {
-                    Acc sum = Acc(0);
-                    for (int gg = 0; gg < kCCG; ++gg) sum += red_c[gg * Rc + i];
-                    const long long row = (long long)ch * Rc + i;
-                    if (row < n && sum != Acc(0)) atomicAdd(Ucur + row, sum);
-                  }
-                  sb.arrive(ch);
-                }
-              } else {
-                Acc d0 = Acc(0), d1 = Acc(0);
-                if (rowok) {
-                  if (cl0 < wl) {
-                    Acc xv[V];
-                    cvt_to<TX, Acc>(*reinterpret_cast<const uint4*>(stg + (size_t)cgl * kSeg), xv);
-#pragma unroll
-                    for (int e = 0; e < V; ++e) d0 = fma(xv[e], ul[e], d0);
-                  }
-                  if (cl1 < wl) {
-                    Acc xv[V];
-                    cvt_to<TX, Acc>(*reinterpret_cast<const uint4*>(stg + (size_t)(cgl + kCCG) * kSeg), xv);
-#pragma unroll
-                    for (int e = 0; e < V; ++e) d1 = fma(xv[e], ul[e], d1);
-                  }
-                }
-                // reduce-scatter over the kCRV row-vector lanes (within a warp):
-                // lanes in the lower half keep column cl0, the upper half cl1
-                const bool hi = (rv & (kCRV / 2)) != 0;
-                Acc dd = (hi ? d1 : d0) + __shfl_xor_sync(0xffffffffu, hi ? d0 : d1, kCRV / 2);
-#pragma unroll
-                for (int o = kCRV / 4; o >= 1; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
-                const int cl = hi ? cl1 : cl0;
-                if ((rv & (kCRV / 2 - 1)) == 0 && cl < wl) tv[cl] += (double)dd;
-              }
-              // the slot is free once every thread has read it
-              if (__syncthreads_or(!ok)) { ok = false; break; }
-              rph ^= 1u << sl;   // the slot's next use waits for the other parity
-              if (warp == 0 && c + NSR < nst) issue(c + NSR);
             }
-            if (!ok) {   // a bounded wait gave up: drain this block's copies in flight
-              if (tid == 0) {
-                atomicCAS(P.err, DERR_NONE, DERR_TIMEOUT);
-                const int ce = c + NSR < nst ? c + NSR : nst;
-                for (int c2 = c; c2 < ce; ++c2) {   // at most one pending phase per slot
-                  const int s2 = (rs0 + c2) % NSR;
-                  tc::mbar_wait(&rfull[s2], (rph >> s2) & 1u, P.timeout);
-                }
-              }
-              __syncthreads();
-              return;
-            }
-            rs0 = (rs0 + nst) % NSR;
+            if (!ok) return;
             slot ^= 1;
             uu[0] = uu_loc;
             block_reduce<1>(uu, rs, kThreads);

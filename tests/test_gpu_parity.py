@@ -220,8 +220,8 @@ def test_chunked_q_apply_f32_matches_oracle(flr):
 
 
 def test_config4_full_size_is_stationary(flr):
-    """Config 4 at full size (250x400 lattice, n=5000, FP16 X, 1 GB; the one-pass chunked
-    Q-apply): too large for the oracle's MM, so the property that holds at any size
+    """Config 4 at full size (250x400 lattice, n=5000, FP16 X, 1 GB, streamed from HBM
+    twice per CG iteration): too large for the oracle's MM, so the property that holds at any size
     is checked instead.  The
     MM limit is a stationary point of f_eps (Lemma 2): the oracle's gradient
     X^T(X b - y) + lam1 A b + lam2 B b at the returned b is ~5e-7 ||X^T y|| for an
