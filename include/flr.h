@@ -320,9 +320,11 @@ flr_status flr_solve_noalloc(const void* Xt, int32_t dtype, int64_t n, int64_t p
  * thread blocks at once, one per SM, which keeps every cooperative solve
  * co-resident: a problem too wide for grid_per_slot blocks (each block's
  * slab of coefficients must fit its shared-memory vectors) takes as many
- * blocks as it needs from that budget, waiting in arrival order until they
- * are free.  A request's X, y and edges are borrowed: they must stay valid
- * until flr_server_wait has returned for it.
+ * blocks as it needs from that budget.  Solves take blocks in arrival order;
+ * while the oldest waiting one cannot run, later ones that fit in the free
+ * blocks may overtake it during its first 2 seconds of waiting.  A request's
+ * X, y and edges are borrowed: they must stay valid until flr_server_wait has
+ * returned for it.
  * ------------------------------------------------------------------------- */
 typedef struct flr_server flr_server;
 typedef flr_server* flr_server_t;

@@ -238,10 +238,10 @@ __device__ __forceinline__ double tile_solve_warp(const BatchParams& P, long lon
   for (int e = 0; e < 4; ++e) {
     const int i = i0 + e;
     const bool ok = i < len;
-    m[e] = ok ? P.lmul[base + i] : 0.0;
-    r[e] = ok ? P.r[base + i] : 0.0;
-    dv[e] = ok ? P.dinv[base + i] : 0.0;
-    const double c = (ok && i + 1 < len) ? -P.wr[base + i] : 0.0;
+    m[e] = ok ? ldcg(P.lmul + base + i) : 0.0;
+    r[e] = ok ? ldcg(P.r + base + i) : 0.0;
+    dv[e] = ok ? ldcg(P.dinv + base + i) : 0.0;
+    const double c = (ok && i + 1 < len) ? -ldcg(P.wr + base + i) : 0.0;
     a[e] = -c * dv[e];
   }
   // forward: lane map y_out = A y_in + B
@@ -362,7 +362,21 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
   }
   bool alive = gb.sync();
   int mm = 0, pcur = 0;
-  auto is_own = [&](long long j) -> bool { return ((j / kTM) % G) == b; };
+  // The per-RHS vector work of a CG iteration is split into units (tile t, RHS k),
+  // t-major; block b owns units [u_lo, u_hi), an equal share (the 128-column tiles
+  // alone do not divide evenly over the blocks: p = 2e4 gives 157 tiles for 152).
+  const long long units = ntiles * (long long)K;
+  const long long u_lo = units * b / G, u_hi = units * (b + 1) / G;
+  auto is_own = [&](long long j, int k) -> bool {
+    const long long u = (j / kTM) * K + k;
+    return u >= u_lo && u < u_hi;
+  };
+  // this block's RHS range [ka, kb) of tile t (empty when ka >= kb)
+  auto unit_range = [&](long long t, int& ka, int& kb) {
+    const long long a = u_lo > t * K ? u_lo : t * K, e = u_hi < (t + 1) * K ? u_hi : (t + 1) * K;
+    ka = (int)(a - t * K);
+    kb = (int)(e - t * K);
+  };
   // In the tile loops below all 32 lanes of a warp share one RHS index k
   // (128 columns per k, a multiple of 32), so per-RHS sums reduce by warp
   // shuffles and one shared-memory atomic per warp.
@@ -641,16 +655,18 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       // (a) S p, p^T S p, and the BF16 slices of p for the owned columns
       for (int f = tid; f < kNRMax; f += kBT) s_psp[f] = 0.0;
       __syncthreads();
-      // warp w takes RHS k = w, w + 8, ...; lane l the columns l + 32u of the
-      // tile, u = 0..3, with every load of the four issued before their use
-      for (long long t = b; t < ntiles; t += G) {
-        for (int k = warp; k < NR; k += kBT / 32) {
-          const bool act = k < K && s_cga[k];     // warp-uniform
+      // this block's units: warp w takes RHS k = ka + w, ka + w + 8, ...; lane l
+      // the columns l + 32u of the tile, u = 0..3, with every load of the four
+      // issued before their use.  Rows k >= K of the P slices stay zero.
+      for (long long t = u_lo / K; t < ntiles && t * K < u_hi; ++t) {
+        int ka, kb;
+        unit_range(t, ka, kb);
+        for (int k = ka + warp; k < kb; k += kBT / 32) {
+          const bool act = s_cga[k];              // warp-uniform
           const double g = act ? s_gam[k] : 0.0;
           const long long ko = (long long)k * p;
           auto pv = [&](long long kk) -> double {
-            if (is_own(kk)) return pc[ko + kk];
-            if (kcg == 0) return ldcg(pc + ko + kk);
+            if (kcg == 0 || is_own(kk, k)) return ldcg(pc + ko + kk);
             return fma(g, ldcg(po + ko + kk), ldcg(P.z + ko + kk));
           };
           double pj[4], la[4], wl[4], wr[4], wu[4], wd[4], nl[4], nr[4], nu[4], nd[4];
@@ -660,12 +676,12 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
             const bool ok = act && j < p;
             const long long o = ko + j;
             const long long col = j % q2;
-            pj[u] = ok ? pc[o] : 0.0;
-            la[u] = ok ? P.la[o] : 0.0;
-            wl[u] = ok ? P.wl[o] : 0.0;
-            wr[u] = ok ? P.wr[o] : 0.0;
-            wu[u] = ok ? P.wu[o] : 0.0;
-            wd[u] = ok ? P.wd[o] : 0.0;
+            pj[u] = ok ? ldcg(pc + o) : 0.0;
+            la[u] = ok ? ldcg(P.la + o) : 0.0;
+            wl[u] = ok ? ldcg(P.wl + o) : 0.0;
+            wr[u] = ok ? ldcg(P.wr + o) : 0.0;
+            wu[u] = ok ? ldcg(P.wu + o) : 0.0;
+            wd[u] = ok ? ldcg(P.wd + o) : 0.0;
             nl[u] = (ok && col != 0) ? pv(j - 1) : 0.0;
             nr[u] = (ok && col != q2 - 1 && j + 1 < p) ? pv(j + 1) : 0.0;
             nu[u] = (ok && j >= q2) ? pv(j - q2) : 0.0;
@@ -694,7 +710,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
               P.Ps[(2LL * NR + k) * P.ldp + j] = l;
             }
           }
-          if (k < K) wadd(&s_psp[k], v_psp);
+          wadd(&s_psp[k], v_psp);
         }
       }
       __syncthreads();
@@ -760,13 +776,20 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       double* loc = s_pen;   // 2*kNRMax partials: r^T z, r^T r
       for (int f = tid; f < 2 * kNRMax; f += kBT) loc[f] = 0.0;
       __syncthreads();
-      for (long long t = b; t < ntiles; t += G) {
+      // this block's units: T for tile t and RHS rows [kq, kq + nq) of U (nq = 32
+      // or 64, covering [ka, kb) and staying inside the NR rows), then the updates
+      for (long long t = u_lo / K; t < ntiles && t * K < u_hi; ++t) {
+        int ka, kb;
+        unit_range(t, ka, kb);
+        if (ka >= kb) continue;
+        const int nq = (kb - ka <= 32 || NR == 32) ? 32 : 64;
+        const int kq = ka + nq <= NR ? ka : NR - nq;
         const int rows = (int)(p - t * kTM < kTM ? p - t * kTM : kTM);
-        if (!tc_tile(tp, P.Xt + t * kTM * P.ldn, P.ldn, rows, 0, P.ldn, P.Us, P.ldn,
-                     (long long)NR * P.ldn, 0, P.ldn, P.ldn, NR)) { alive = false; break; }
-        tmem_to_smem(tp.tmem, ts, NR);
+        if (!tc_tile(tp, P.Xt + t * kTM * P.ldn, P.ldn, rows, 0, P.ldn, P.Us + (long long)kq * P.ldn, P.ldn,
+                     (long long)NR * P.ldn, 0, P.ldn, P.ldn, nq)) { alive = false; break; }
+        tmem_to_smem(tp.tmem, ts, nq);
         const bool jac = P.precond == PC_JACOBI;
-        for (int k = warp; k < K; k += kBT / 32) {   // as in (a): warp per RHS, 4 columns per lane
+        for (int k = ka + warp; k < kb; k += kBT / 32) {   // as in (a): warp per RHS, 4 columns per lane
           if (!s_cga[k]) continue;                  // warp-uniform
           const double nu = s_nu[k];
           const long long ko = (long long)k * p;
@@ -776,11 +799,11 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
             const long long j = t * kTM + lane + 32 * u;
             const bool ok = j < p;
             const long long o = ko + j;
-            qv[u] = ok ? P.q[o] : 0.0;
-            pv4[u] = ok ? pc[o] : 0.0;
-            xv[u] = ok ? P.x[o] : 0.0;
-            rv[u] = ok ? P.r[o] : 0.0;
-            iv[u] = (ok && jac) ? P.idg[o] : 0.0;
+            qv[u] = ok ? ldcg(P.q + o) : 0.0;
+            pv4[u] = ok ? ldcg(pc + o) : 0.0;
+            xv[u] = ok ? ldcg(P.x + o) : 0.0;
+            rv[u] = ok ? ldcg(P.r + o) : 0.0;
+            iv[u] = (ok && jac) ? ldcg(P.idg + o) : 0.0;
           }
           double v_rz = 0.0, v_rr = 0.0;
 #pragma unroll
@@ -789,7 +812,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
             const long long j = t * kTM + cl;
             if (j < p) {
               const long long o = ko + j;
-              const double tj = (double)ts[k * kTM + cl];
+              const double tj = (double)ts[(k - kq) * kTM + cl];
               const double qj = tj + qv[u];
               P.x[o] = fma(nu, pv4[u], xv[u]);
               const double rj = fma(-nu, qj, rv[u]);
@@ -807,7 +830,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         }
         __syncthreads();
         if (P.precond != PC_JACOBI) {
-          for (int k = tid >> 5; k < K; k += kBT / 32)   // one warp per RHS
+          for (int k = ka + (tid >> 5); k < kb; k += kBT / 32)   // one warp per RHS
             if (s_cga[k]) {
               const double rz = tile_solve_warp(P, k, t * kTM, rows, nullptr);
               if ((tid & 31) == 0) atomicAdd(&loc[k], rz);
@@ -829,8 +852,10 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       __syncthreads();
       {
         double* pn = pcur ? P.pb0 : P.pb1;
-        for (long long t = b; t < ntiles; t += G)
-          for (int k = warp; k < K; k += kBT / 32) {
+        for (long long t = u_lo / K; t < ntiles && t * K < u_hi; ++t) {
+          int ka, kb;
+          unit_range(t, ka, kb);
+          for (int k = ka + warp; k < kb; k += kBT / 32) {
             if (!s_cga[k]) continue;                // warp-uniform
             const double g = s_gam[k];
             const long long ko = (long long)k * p;
@@ -838,8 +863,8 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const long long j = t * kTM + lane + 32 * u;
-              pv4[u] = j < p ? pc[ko + j] : 0.0;
-              zv[u] = j < p ? P.z[ko + j] : 0.0;
+              pv4[u] = j < p ? ldcg(pc + ko + j) : 0.0;
+              zv[u] = j < p ? ldcg(P.z + ko + j) : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -847,6 +872,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
               if (j < p) pn[ko + j] = fma(g, pv4[u], zv[u]);
             }
           }
+        }
       }
       pcur ^= 1;
       ++kcg;

@@ -17,6 +17,8 @@
 
 namespace {
 
+constexpr double kBackfill = 2.0;   // seconds a waiting solve may be overtaken
+
 struct Job {
   uint64_t id;
   flr_request r;
@@ -50,9 +52,14 @@ struct flr_server {
   std::unordered_map<uint64_t, bool> pending;   // submitted, not yet finished
   int64_t in_use = 0;
   // thread blocks of the device the server's cooperative solves may hold at once
-  // (slots x grid_per_slot <= #SMs, one block per SM): taken in ticket order
+  // (slots x grid_per_slot <= #SMs, one block per SM).  Solves take them in
+  // arrival order; while the oldest waiting solve cannot run, a later one that
+  // fits in the free blocks may go first, for at most kBackfill seconds of the
+  // oldest one's wait (so it is never starved).
+  struct Waiter { uint64_t ticket; int need; double since; };
   int blocks_free = 0, blocks_total = 0;
-  uint64_t ticket_next = 0, ticket_serving = 0;
+  uint64_t ticket_next = 0;
+  std::deque<Waiter> waiting;
   std::condition_variable cv_blocks;
   uint64_t next_id = 1;
   bool stopping = false;
@@ -178,9 +185,18 @@ void flr_server::worker(int slot) {
       {
         std::unique_lock<std::mutex> lk(mu);
         const uint64_t t = ticket_next++;
-        cv_blocks.wait(lk, [&] { return ticket_serving == t && blocks_free >= need; });
+        waiting.push_back(Waiter{t, need, now()});
+        auto can_go = [&] {
+          if (blocks_free < need) return false;
+          const Waiter& head = waiting.front();
+          if (head.ticket == t) return true;
+          return head.need > blocks_free && now() - head.since < kBackfill;
+        };
+        // timed waits: the backfill window closes without a notification
+        while (!can_go()) cv_blocks.wait_for(lk, std::chrono::milliseconds(50));
         blocks_free -= need;
-        ++ticket_serving;
+        for (auto it = waiting.begin(); it != waiting.end(); ++it)
+          if (it->ticket == t) { waiting.erase(it); break; }
       }
       cv_blocks.notify_all();
       st = gmin < 0 ? FLR_ENOTIMPL
