@@ -221,7 +221,10 @@ flr_status flr_solve(flr_t h, double lambda1, double lambda2, double eps, double
  * BF16 X on a chain or lattice with precond AUTO, JACOBI, TRIDIAG or PAPER
  * runs one tensor-core launch per 64 pairs (AUTO: the per-tile tridiagonal
  * preconditioner); any other case solves the pairs one after another with
- * flr_solve. */
+ * flr_solve.  The first tensor-core batch on a handle also tunes the launch:
+ * it times one capped launch (one MM iteration, 24 CG iterations) for each of
+ * up to three split-K chunk lengths of the X P contraction and keeps the
+ * fastest for the handle's later batches. */
 flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const double* lambda2,
                            double eps, double tol, const flr_opts* opts, double* betas,
                            int32_t io_mem, double* objectives, flr_stats* stats);

@@ -119,6 +119,11 @@ struct flr_handle {
   long long ldp = 0;
   int bS = 1;
   long long bkchunk = 0;
+  // split-K candidates of the batched phase A (columns per chunk), timed on the
+  // first flr_solve_batch of the handle; batch_tuned once the choice is made
+  long long bcand[3] = {0, 0, 0};
+  int bncand = 0;
+  bool batch_tuned = false;
   __nv_bfloat16* Xr = nullptr;
   double* bvec[15] = {nullptr};
   __nv_bfloat16 *Ps = nullptr, *Us = nullptr;
@@ -313,19 +318,31 @@ flr_status batch_prepare(flr_handle* h) {
   const long long n = h->n, p = h->p;
   h->ldp = (p + 7) / 8 * 8;
   const long long mtiles = (n + kTM - 1) / kTM;
+  // phase A splits the reduction over p into S chunks so that about one work item
+  // (row tile, chunk) falls to each SM; the autotuner also tries half and twice
+  // that chunk length
   int S = (int)std::max<long long>(1, (long long)h->sm_count / mtiles);
   long long kchunk = (h->ldp + S - 1) / S;
   kchunk = (kchunk + 63) / 64 * 64;
   S = (int)((h->ldp + kchunk - 1) / kchunk);
   h->bS = S;
   h->bkchunk = kchunk;
+  int Smax = S;
+  h->bncand = 0;
+  for (long long kc : {kchunk, (kchunk / 2 + 63) / 64 * 64, kchunk * 2}) {
+    bool dup = kc < 64 || (kc > h->ldp && kc != kchunk);
+    for (int i = 0; i < h->bncand; ++i) dup = dup || ((h->ldp + kc - 1) / kc == (h->ldp + h->bcand[i] - 1) / h->bcand[i]);
+    if (dup) continue;
+    h->bcand[h->bncand++] = kc;
+    Smax = std::max<int>(Smax, (int)((h->ldp + kc - 1) / kc));
+  }
   if ((s = dalloc(h, &h->Xr, (size_t)(n * h->ldp))) != FLR_OK) return s;
   for (int i = 0; i < 15; ++i)
     if ((s = dalloc(h, &h->bvec[i], (size_t)kNRMax * p)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->Ps, (size_t)kSlices * kNRMax * h->ldp)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->Us, (size_t)kSlices * kNRMax * h->ldn)) != FLR_OK) return s;
-  if ((s = dalloc(h, &h->Upart, (size_t)S * kNRMax * n)) != FLR_OK) return s;
-  if ((s = dalloc(h, &h->U0part, (size_t)S * kNRMax * n)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->Upart, (size_t)Smax * kNRMax * n)) != FLR_OK) return s;
+  if ((s = dalloc(h, &h->U0part, (size_t)Smax * kNRMax * n)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->U0, (size_t)kNRMax * n)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->bred, (size_t)kRedSlots * 4 * kNRMax)) != FLR_OK) return s;
   if ((s = dalloc(h, &h->blam, (size_t)2 * kNRMax)) != FLR_OK) return s;
@@ -342,6 +359,44 @@ flr_status batch_prepare(flr_handle* h) {
       reinterpret_cast<unsigned short*>(h->Xr), h->ldp);
   FLR_TRY(cudaGetLastError());
   h->batch_ready = true;
+  return FLR_OK;
+}
+
+flr_status batch_group(flr_handle* h, int K, const double* l1, const double* l2, double eps,
+                       double tol, const flr_opts& o, double* betas, int io_mem,
+                       double* objectives, flr_stats* stats);
+
+// The autotuner: on the first batched solve of a handle, time one launch per
+// split-K candidate (one MM iteration, its FP64 passes and kTuneCG lockstep CG
+// iterations of the caller's first RHS group and options) and keep the fastest.
+constexpr int kTuneCG = 24;
+flr_status batch_tune(flr_handle* h, int K, const double* l1, const double* l2, double eps, double tol,
+                      const flr_opts& o) {
+  flr_status s = batch_prepare(h);
+  if (s != FLR_OK || h->batch_tuned) return s;
+  h->batch_tuned = true;
+  if (h->bncand <= 1) return FLR_OK;
+  flr_opts t = o;
+  t.max_mm = 1;
+  t.max_cg = kTuneCG;
+  t.min_cg = kTuneCG;
+  t.tol_cg = 1e-300;
+  t.tol_cg_rel = 0.0;
+  t.max_refine = 0;
+  std::vector<double> b((size_t)K * h->p);
+  std::vector<flr_stats> st((size_t)K);
+  float best = 0.f;
+  long long kbest = h->bkchunk;
+  for (int c = 0; c < h->bncand; ++c) {
+    h->bkchunk = h->bcand[c];
+    h->bS = (int)((h->ldp + h->bkchunk - 1) / h->bkchunk);
+    s = batch_group(h, K, l1, l2, eps, tol, t, b.data(), FLR_MEM_HOST, nullptr, st.data());
+    if (s == FLR_EINVAL || s == FLR_ECUDA || s == FLR_ENOMEM || s == FLR_ENOTIMPL || s == FLR_ETIMEOUT)
+      return s;
+    if (c == 0 || st[0].ms < best) { best = (float)st[0].ms; kbest = h->bkchunk; }
+  }
+  h->bkchunk = kbest;
+  h->bS = (int)((h->ldp + kbest - 1) / kbest);
   return FLR_OK;
 }
 
@@ -778,7 +833,8 @@ flr_status flr_solve_batch(flr_t h, int32_t K, const double* lambda1, const doub
                        (o.precond == FLR_PC_AUTO || o.precond == FLR_PC_JACOBI ||
                         o.precond == FLR_PC_TRIDIAG || o.precond == FLR_PC_PAPER);
   if (tc_path) {
-    flr_status first = FLR_OK;
+    flr_status first = batch_tune(h, std::min(kNRMax, (int)K), lambda1, lambda2, eps, tol, o);
+    if (first != FLR_OK) return first;
     for (int k0 = 0; k0 < K; k0 += kNRMax) {
       const int kg = std::min(kNRMax, K - k0);
       flr_status s = batch_group(h, kg, lambda1 + k0, lambda2 + k0, eps, tol, o,

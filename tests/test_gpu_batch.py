@@ -111,7 +111,8 @@ def test_batch_mid_size_iterates_match_oracle(flr):
     At this size the tensor-core pipeline runs its real code paths: phase C
     reduces over n = 512 in 8 chunks of 64, more than its 3 stages, so every
     tile recycles stages through the mbarrier waits and parity flips, and
-    phase A splits p over 27 chunks of 192 per 128-row tile.  Each surrogate
+    phase A splits p over 14 to 40 chunks per 128-row tile (the autotuner
+    times 27 chunks of 192 and half and twice that length).  Each surrogate
     is solved to an FP64 true residual of 1e-12 (max_refine), so the GPU's
     iterates follow the exact MM map."""
     import json, os
