@@ -461,6 +461,11 @@ __device__ __forceinline__ void phase_a(const SolveParams& P, const TX* __restri
 #pragma unroll
         for (int k = 0; k < kLA; ++k) raw[k] = ldx<TX>(Xt, xs, wt, ws, P.ldn, j0, j + k, off);
 #pragma unroll
+        for (int k = 0; k < kLA; ++k) {   // the next group's streamed columns into L2
+          const int jn = j + kLA + k;
+          if (jn < wl && jn - wt >= ws) prefetch_l2(Xt + (j0 + jn) * P.ldn + off);
+        }
+#pragma unroll
         for (int k = 0; k < kLA; ++k) {
           A xv[V];
           cvt_to<TX, A>(raw[k], xv);
@@ -554,6 +559,14 @@ __device__ __forceinline__ void phase_c(const SolveParams& P, const TX* __restri
           const int rv = rv0 + 32 * u;
           if (base + c < wl && rv < nv)
             raw[c][u] = ldx<TX>(Xt, xs, wt, ws, P.ldn, j0, base + c, (long long)rv * V);
+        }
+#pragma unroll
+      for (int c = 0; c < CPW; ++c)   // the next round's streamed rows into L2
+#pragma unroll
+        for (int u = 0; u < UR; ++u) {
+          const int rvn = rv0 + 32 * (UR + u);
+          if (base + c < wl && base + c - wt >= ws && rvn < nv)
+            prefetch_l2(Xt + (j0 + base + c) * P.ldn + (long long)rvn * V);
         }
 #pragma unroll
       for (int u = 0; u < UR; ++u) {
