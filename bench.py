@@ -13,6 +13,7 @@ shard), each rank on its own dataset seed; value = all ranks' solves / max time.
 """
 import argparse
 import hashlib
+import re
 import json
 import os
 import subprocess
@@ -110,13 +111,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def strip_comments(src):
+    """C++ source without its // and /* */ comments and blank lines (what compiles)."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(l.rstrip() for l in src.splitlines() if l.strip())
+
+
 def kernel_source_hash():
-    """Hash of the sources the single-problem solve kernel is built from."""
+    """Hash of the code (comments stripped) the single-problem solve kernel is built from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1306_1970_gb300", "csrc")
     for fn in ("flr_device.cuh", "flr_solve.cuh"):
-        with open(os.path.join(csrc, fn), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, fn), encoding="utf-8") as fh:
+            h.update(strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

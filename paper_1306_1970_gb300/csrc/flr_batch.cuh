@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
       if (ncga == 0) break;
       const double* pc = pcur ? P.pb1 : P.pb0;
       const double* po = pcur ? P.pb0 : P.pb1;
-      // (a) S p, p^T S p, and the BF16 slices of p for the owned columns
+      // (a) S p, p^T S p, and the BF16 slices of p for this block's units
       for (int f = tid; f < kNRMax; f += kBT) s_psp[f] = 0.0;
       __syncthreads();
       // this block's units: warp w takes RHS k = ka + w, ka + w + 8, ...; lane l
@@ -772,7 +772,7 @@ __global__ void __launch_bounds__(kBT, 1) mm_batch_kernel(const BatchParams P) {
         s_nu[k] = nu;
       }
       __syncthreads();
-      // (d) phase C: T = X^T U for the owned tiles (tensor cores), then the updates
+      // (d) phase C: T = X^T U for this block's units (tensor cores), then the updates
       double* loc = s_pen;   // 2*kNRMax partials: r^T z, r^T r
       for (int f = tid; f < 2 * kNRMax; f += kBT) loc[f] = 0.0;
       __syncthreads();

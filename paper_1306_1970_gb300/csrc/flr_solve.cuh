@@ -89,7 +89,7 @@ constexpr double kStrong = 16.0;   // strong-edge threshold of PC_TWOLEVEL
 
 constexpr int kRF = 3;   // fields per block reduction
 constexpr int kLA = 16;  // 16-byte X loads in flight per thread in phase A
-// One-pass (chunked) Q-apply for X larger than L2: row chunks of kCRV 16-byte
+// One-pass (chunked) Q-apply (x_smem = 1): row chunks of kCRV 16-byte
 // row vectors, kCCG column groups.
 constexpr int kCRV = 16;
 constexpr int kCCG = kThreads / kCRV;
@@ -1602,7 +1602,7 @@ __device__ __forceinline__ void mm_solve_body(const SolveParams& P, uint32_t tme
 
 // The solve kernel: the body above, with TMEM allocated around it when the
 // plan keeps X columns there (tct > 0).  CH selects the chunked one-pass
-// Q-apply (for X larger than L2; P.chunked must be set).  Every return of the body comes back
+// Q-apply (x_smem = 1; P.chunked must be set).  Every return of the body comes back
 // here, so TMEM is released on every path.  One CTA per SM (launch bounds and
 // registers), so the 512-column allocation never waits for another CTA of
 // this kernel.
