@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--stream-requests", type=int, default=16,
                     help="served-stream requests in the bench line (0 = skip)")
     ap.add_argument("--stream-rate", type=float, default=1.0, help="offered requests/s")
+    ap.add_argument("--stream-slots", type=int, default=8,
+                    help="server slots of the served-stream leg (8 x 19 blocks: half the p50 "
+                         "latency of 4 x 38 on its 16 requests, the same fits/s)")
     ap.add_argument("--stream-max-mm", type=int, default=3000,
                     help="MM-iteration cap of each served fit in the bench line")
     ap.add_argument("--once", default=None, choices=["config2", "config4", "hbm4", "batch3", "chain3", "serve5", "stream"],
@@ -453,7 +456,7 @@ def served_stream_leg(args, dev):
     of the served-stream recipe (p log-uniform in [500, --p-hi], n = p/4, FP32 or BF16
     X, chain / lattice / 5-NN, lambdas log-uniform in [1e-3, 1]), inputs generated on
     the GPU before the clock starts, offered open-loop as Poisson arrivals at
-    --stream-rate requests/s to a --slots-slot server.  Each fit stops at the bench's
+    --stream-rate requests/s to a --stream-slots-slot server.  Each fit stops at the bench's
     tol or after --stream-max-mm MM iterations (status 4, reported with its est_err).
     Latency is submit to result; fits/s is requests / (first submit to last result)."""
     import threading
@@ -468,7 +471,7 @@ def served_stream_leg(args, dev):
             X = X.view(torch.int16)
         data.append((r, X, y, g))
     torch.cuda.synchronize()
-    srv = flr.Server(slots=args.slots)
+    srv = flr.Server(slots=args.stream_slots)
     ids = [None] * len(data)
     start = time.perf_counter()
 
@@ -490,7 +493,7 @@ def served_stream_leg(args, dev):
     lat = [rr.t_end - rr.t_submit for rr in res]
     st = [rr.status for rr in res]
     capped = [rr.stats.est_err for rr in res if rr.status == 4]
-    return {"requests": len(res), "offered_rate_per_s": args.stream_rate, "slots": args.slots,
+    return {"requests": len(res), "offered_rate_per_s": args.stream_rate, "slots": args.stream_slots,
             "p_range": [500, args.p_hi], "fits_per_s": len(res) / wall, "seconds": wall,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "status_ok": int(sum(1 for x in st if x == 0)),
