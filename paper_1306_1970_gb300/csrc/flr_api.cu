@@ -878,7 +878,8 @@ int flr_min_grid(flr_t h) {
     const long long w = (h->p + G - 1) / G;
     if (w > 8192) continue;
     const long long wpad = (w + 3) / 4 * 4;
-    if (solve_smem_bytes(h->ldn, wpad, V, halo_entries(wpad, q2p, h->p), trows) <= (size_t)dyn_max)
+    // (the margin covers the other kernel instances' slightly different static shared memory)
+    if (solve_smem_bytes(h->ldn, wpad, V, halo_entries(wpad, q2p, h->p), trows) + 1024 <= (size_t)dyn_max)
       return (int)G;
   }
   return -1;
