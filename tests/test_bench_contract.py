@@ -28,3 +28,15 @@ def test_reference_arm_prints_the_contract_line():
     assert "217 such iterations" in d["cpu_baseline"]["sample"]
     assert d["config"]["step"] == "1 MM iteration of the oracle"
     assert abs(d["value"] * d["ms_per_step"] / 1000.0 * 217 - 1.0) < 1e-9
+
+
+def test_kernel_hash_ignores_comments_only():
+    """The committed ncu traffic is keyed by a hash of the solve kernel's code with
+    comments stripped: a comment edit keeps it, a code edit changes it."""
+    import bench
+    a = "int x = 1;  // one\n/* block\n comment */\nint y = 2;\n"
+    b = "int x = 1;\n\n// another comment\nint y = 2;   \n"
+    c = "int x = 1;\nint y = 3;\n"
+    assert bench.strip_comments(a) == bench.strip_comments(b) == "int x = 1;\nint y = 2;"
+    assert bench.strip_comments(c) != bench.strip_comments(a)
+    assert len(bench.kernel_source_hash()) == 16
