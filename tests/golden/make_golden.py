@@ -4,7 +4,8 @@ Calls only oracle/ and flr_inputs/.  Each case is written to
 tests/golden/<name>.json:  the converged MM objective f and f_eps, the
 iteration count, the final relative change, input fingerprints (so a changed
 generator is caught before a parity comparison) and beta (all of it for
-p <= 100000, otherwise 512 sampled indices plus max |beta|).
+p <= 100000, otherwise 512 sampled indices plus max |beta|; none for the
+config2_s<seed> cases, which only the objective gap uses).
 
 Cases whose name ends in _r<R> hold the MM iterate after exactly R
 iterations of Algorithm 1 from its initialisation (no stop test), beta(R)
@@ -58,6 +59,8 @@ def cases():
         "denoise256": (lambda: fi.denoise(lam2=0.1), "identity", None),
         "denoise256_r30": (lambda: fi.denoise(lam2=0.1), "identity", None),
         "denoise256_l1_r30": (lambda: fi.denoise(lam2=1.0), "identity", None),
+        # the bench workload's other dataset seeds (objective only, no beta)
+        **{f"config2_s{s}": ((lambda s=s: fi.config(2, s=s)), "woodbury", "nobeta") for s in range(1, 10)},
     }
 
 
@@ -74,7 +77,7 @@ def fixed_iterations(name):
     return int(tail[1:]) if tail.startswith("r") and tail[1:].isdigit() else None
 
 
-def solve(pr, solver, lam1, lam2, log=None, fixed=None):
+def solve(pr, solver, lam1, lam2, log=None, fixed=None, keep_beta=True):
     E = pr.graph.edges
     t = time.time()
     if solver == "identity":
@@ -99,7 +102,9 @@ def solve(pr, solver, lam1, lam2, log=None, fixed=None):
         out["fixed_iterations"] = fixed
     b = r.beta
     out["beta_absmax"] = float(np.abs(b).max())
-    if b.shape[0] <= 100000:
+    if not keep_beta:
+        pass
+    elif b.shape[0] <= 100000:
         out["beta"] = [float(v) for v in b]
     else:
         idx = np.sort(np.random.default_rng(0).choice(b.shape[0], 512, replace=False))
@@ -129,7 +134,7 @@ def make(name):
         rec["solutions"] = [solve(pr, solver, float(pr.lam_grid[i, 0]), float(pr.lam_grid[i, 1]),
                                   sys.stdout, R) for i in GRID8]
     else:
-        rec.update(solve(pr, solver, pr.lam1, pr.lam2, sys.stdout, R))
+        rec.update(solve(pr, solver, pr.lam1, pr.lam2, sys.stdout, R, keep_beta=lam != "nobeta"))
     with open(os.path.join(HERE, name + ".json"), "w") as fh:
         # large vectors on one line each
         json.dump(rec, fh, indent=None if pr.p > 4096 else 1)

@@ -276,6 +276,24 @@ def test_config2_full_size(flr):
     print(f"limit: mm={st.mm_iters} (oracle {g['iters']}), max|dbeta|/|beta|inf = {db:.2e}")
 
 
+@pytest.mark.parametrize("seed", range(10))
+def test_bench_stop_settings_across_seeds(flr, seed):
+    """The bench's stop settings (tol 3e-9, tol_cg 1e-7, adaptive inner tolerance
+    10) on the bench workload's dataset seeds 0-9 meet the 1e-6 objective gap
+    against each seed's converged oracle solution, and est_err is not below the
+    measured gap."""
+    g = golden("config2" if seed == 0 else f"config2_s{seed}")
+    pr = fi.config(2, s=seed)
+    check_fingerprint(pr, g)
+    prob = problem(flr, pr)
+    _, st = prob.solve(pr.lam1, pr.lam2, eps=pr.eps, tol=3e-9, tol_cg=1e-7, tol_cg_rel=10.0,
+                       max_mm=20000)
+    gap = abs(st.f - g["f"]) / g["f"]
+    print(f"seed {seed}: gap={gap:.2e} mm={st.mm_iters} cg={st.cg_iters} {st.ms:.1f} ms")
+    assert st.status == 0 and gap <= GAP, (gap, st)
+    assert st.est_err >= gap, (st.est_err, gap)
+
+
 @pytest.mark.parametrize("p", [1000, 10000])
 def test_paper_c1_mm_iterations_match_table_c1(flr, p):
     """Scenario C1 of Section 5 regenerated (n = 1000, FP64 X, eps = 1e-8, stop at a
